@@ -1,0 +1,169 @@
+/* hsk.h -- C ABI of a single-GPU sorting-based k-mer counter (HySortK,
+ * arXiv 2407.07718), written for NVIDIA GB300 (sm_103a).
+ *
+ * What is computed (Sec. 2.1 k-mer counting; Sec. 3.1 sorting-based counting):
+ * for every read and every window of k consecutive bases that are all
+ * upper-case A, C, G or T, the canonical k-mer -- the numeric minimum of the
+ * window's 2-bit code (A=0 C=1 G=2 T=3, first base most significant) and the
+ * code of its reverse complement -- is counted.  The result is
+ *   - every distinct canonical k-mer whose count c satisfies lo <= c <= hi,
+ *     with c, in ascending key order (the frequency filter of Sec. 3.1 and
+ *     Sec. 4; the paper uses lo=2, hi=50);
+ *   - the histogram over ALL distinct k-mers before the filter: hist[c] is the
+ *     number of distinct k-mers seen exactly c times, for 1 <= c < hist_len-1;
+ *     hist[hist_len-1] collects every count >= hist_len-1; hist[0] = 0.
+ * Any other byte (N, lower case, IUPAC codes) breaks every window containing
+ * it.  Windows never cross a read boundary.  Counts are exact (Sec. 3.3).
+ *
+ * How (all on the GPU, no CPU fallback): 2-bit encoding (Sec. 2.2); canonical
+ * k-mers with hash-scored minimizers and supermers (Sec. 3.2); supermers
+ * scattered into minimizer-hashed buckets, the paper's tasks (Sec. 3.4);
+ * an LSD radix sort of packed keys (Sec. 3.1); a run-length scan with the
+ * filter and histogram (Sec. 3.1).
+ *
+ * Keys: k <= 32 -> one uint64 word per k-mer (the 2k-bit code, right
+ * aligned); 33 <= k <= 64 -> two uint64 words per k-mer, little-endian
+ * {lo, hi} of the 2k-bit code.
+ *
+ * Errors: every function returns HSK_OK (0) or a negative HSK_E* code;
+ * hsk_last_error() then holds a one-line description.  A context is not
+ * thread-safe: use one context per host thread.
+ */
+#ifndef HSK_H
+#define HSK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HSK_OK 0
+#define HSK_EINVAL (-1)     /* bad argument: k, m, lo/hi, pointers, offsets */
+#define HSK_ENOMEM (-2)     /* the job does not fit the context's HBM budget */
+#define HSK_ECUDA (-3)      /* a CUDA runtime call failed; see hsk_last_error */
+#define HSK_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define HSK_ECANCELED (-5)  /* the job was cancelled before it ran */
+#define HSK_EOVERFLOW (-6)  /* a count or size exceeds the representable range */
+#define HSK_ENOTFOUND (-7)  /* unknown ticket */
+
+typedef struct hsk_ctx hsk_ctx;
+
+/* Context configuration.  Fill with hsk_config_default() and override. */
+typedef struct {
+    int device;            /* CUDA device ordinal */
+    uint64_t hbm_budget;   /* bytes of device memory the context may hold; 0 = 90 % of free */
+    uint32_t hist_len;     /* histogram bins, >= 2 (default 65536) */
+    uint32_t n_buckets;    /* minimizer buckets (tasks); 0 = chosen per job */
+    uint32_t radix_bits;   /* LSD digit width, 8 (default) */
+    uint32_t max_chunk_kmers; /* 0 = as many as the budget allows; else cap per sort chunk */
+    uint64_t seed;         /* XOR-ed into each canonical m-mer before hashing */
+    int autotune;          /* 1 = pick bucket count and chunking per job */
+} hsk_config;
+
+/* A counting result.  All arrays are owned by the context and stay valid until
+ * the next counting call on the same context, hsk_release() of its ticket, or
+ * hsk_destroy().  For hsk_count() they are host pointers; for
+ * hsk_count_device() they are device pointers (kmers, counts, hist). */
+typedef struct {
+    uint64_t n_pairs;        /* entries in kmers/counts */
+    const uint64_t* kmers;   /* n_pairs * key_words words, ascending */
+    const uint32_t* counts;  /* n_pairs counts, each in [lo, hi] */
+    const uint64_t* hist;    /* hist_len bins (see above) */
+    uint32_t hist_len;
+    int key_words;           /* 1 for k <= 32, 2 for 33 <= k <= 64 */
+    uint64_t n_windows;      /* valid k-mer windows counted (sum of all counts) */
+    uint64_t n_distinct;     /* distinct canonical k-mers */
+    uint32_t max_count;      /* largest count of any k-mer */
+    uint32_t n_chunks;       /* sort chunks the job was split into */
+    uint64_t n_supermers;    /* supermer records formed */
+    double device_ms;        /* device time of the job (CUDA events), ms */
+} hsk_result;
+
+/* One job for the batched and served forms: host pointers, borrowed until the
+ * call returns (hsk_count_batch) or the job completes (hsk_submit). */
+typedef struct {
+    const char* reads;        /* ASCII bases of all reads, concatenated */
+    const uint64_t* offsets;  /* n_reads + 1 entries, offsets[0] = 0, non-decreasing */
+    uint64_t n_reads;
+    int k;                    /* 1 <= k <= 64 */
+    int m;                    /* 1 <= m <= min(k, 32) */
+    uint32_t lo, hi;          /* inclusive count filter, lo <= hi */
+} hsk_job;
+
+/* Defaults: device 0, budget 0 (90 % of free), hist_len 65536, buckets auto,
+ * 8-bit digits, seed 0x9E3779B97F4A7C15, autotune on. */
+int hsk_config_default(hsk_config* cfg);
+
+/* Create a context on cfg->device (cfg = NULL: defaults).  *out receives the
+ * context; on failure *out is NULL and the code says why. */
+int hsk_create(hsk_ctx** out, const hsk_config* cfg);
+
+/* Release every device and host buffer of the context.  NULL-safe. */
+void hsk_destroy(hsk_ctx* ctx);
+
+/* One-line description of the last error on this context ("" if none).  The
+ * string belongs to the context. */
+const char* hsk_last_error(hsk_ctx* ctx);
+
+/* Count canonical k-mers of host-resident reads.  reads[offsets[i] ..
+ * offsets[i+1]) is read i; offsets has n_reads + 1 non-decreasing entries
+ * starting at 0.  Host-to-device copies, the GPU pipeline and the
+ * device-to-host copies of the result all happen inside the call; the result
+ * arrays are host memory owned by the context.
+ * Errors: HSK_EINVAL (k outside [1,64], m outside [1, min(k,32)], lo > hi,
+ * NULL pointer with n_reads > 0, offsets not monotone or not starting at 0),
+ * HSK_ENOMEM, HSK_ECUDA, HSK_ETIMEOUT. */
+int hsk_count(hsk_ctx* ctx, const char* reads, const uint64_t* offsets, uint64_t n_reads, int k,
+              int m, uint32_t lo, uint32_t hi, hsk_result* out);
+
+/* As hsk_count, but reads (n_bases bytes) and offsets (n_reads + 1 entries)
+ * are device pointers, the work is ordered on `stream` (a cudaStream_t; NULL
+ * = legacy default stream), and the result arrays are device memory owned by
+ * the context.  Returns after the result is complete.  Offsets are checked on
+ * the device; a violation returns HSK_EINVAL. */
+int hsk_count_device(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offsets,
+                     uint64_t n_reads, uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi,
+                     void* stream, hsk_result* out);
+
+/* Copy the arrays of a result (as returned by any counting call on this
+ * context) into caller memory: kmers_dst n_pairs * key_words words,
+ * counts_dst n_pairs words, hist_dst hist_len words; any destination may be
+ * NULL to skip it.  dst_on_device = 1 when the destinations are device
+ * pointers.  Ordered on `stream` and complete on return. */
+int hsk_result_copy(hsk_ctx* ctx, const hsk_result* res, uint64_t* kmers_dst, uint32_t* counts_dst,
+                    uint64_t* hist_dst, int dst_on_device, void* stream);
+
+/* Batched form: count n_jobs independent host-resident read sets.  Small
+ * jobs are packed together and counted by shared launches captured in a CUDA
+ * graph; each outs[i] is bit-identical to what hsk_count() returns for jobs[i]
+ * alone.  Result arrays are host memory owned by the context, valid until the
+ * next counting call.  Errors as hsk_count; on error no result is valid. */
+int hsk_count_batch(hsk_ctx* ctx, const hsk_job* jobs, uint32_t n_jobs, hsk_result* outs);
+
+/* Served form (continuous batching).  hsk_submit queues a job and returns a
+ * ticket at once; a worker thread admits queued jobs while the device memory
+ * they need fits the budget, runs admitted jobs concurrently on their own
+ * streams, and completes them in any order.  Inputs stay borrowed until the
+ * job completes.  hsk_poll sets *done to 1 when the ticket's job finished;
+ * hsk_wait blocks until then and fills *out (host arrays owned by the context,
+ * valid until hsk_release(ticket)); hsk_cancel withdraws a job that has not
+ * started (its wait then returns HSK_ECANCELED).  The submit API may be
+ * called from any host thread. */
+int hsk_submit(hsk_ctx* ctx, const hsk_job* job, uint64_t* ticket);
+int hsk_poll(hsk_ctx* ctx, uint64_t ticket, int* done);
+int hsk_wait(hsk_ctx* ctx, uint64_t ticket, hsk_result* out);
+int hsk_cancel(hsk_ctx* ctx, uint64_t ticket);
+int hsk_release(hsk_ctx* ctx, uint64_t ticket);
+
+/* Latency of a completed served job: *queued_s = seconds from hsk_submit to
+ * admission, *run_s = seconds from admission to completion.  HSK_EINVAL if
+ * the job has not completed, HSK_ENOTFOUND for an unknown ticket. */
+int hsk_ticket_times(hsk_ctx* ctx, uint64_t ticket, double* queued_s, double* run_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSK_H */

@@ -1,0 +1,115 @@
+/* hsk_stages.h -- per-stage entry points of the k-mer counting pipeline.
+ *
+ * Each function runs ONE stage of the pipeline that hsk_count() runs end to
+ * end, on device-resident inputs, so that each stage can be checked on its
+ * own.  All pointers named d_* are device pointers; `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Each function returns after
+ * its work on `stream` is complete.  Caller-provided outputs must have the
+ * sizes stated; context-owned outputs stay valid until the next call on the
+ * same context.  Return codes are those of hsk.h.
+ *
+ * Device layouts (shared by all stages):
+ *   packed 2-bit bases : uint64 words, 32 bases per word, base g in bits
+ *                        [63-2(g%32)-1 .. 63-2(g%32)] of word g/32 (first
+ *                        base most significant); A=0 C=1 G=2 T=3; invalid
+ *                        bytes are stored as 0.
+ *   bit masks          : uint64 words, 64 bases per word, base g at bit
+ *                        63-(g%64) of word g/64.
+ *   supermer record    : record_words uint64 words (2 for k <= 32, 4 for
+ *                        k <= 64); the supermer's bases packed from the most
+ *                        significant bit of word 0 onward, bases beyond the
+ *                        supermer zero; the low 8 bits of the last word hold
+ *                        the number of k-mers n; the record spans n + k - 1
+ *                        bases.
+ */
+#ifndef HSK_STAGES_H
+#define HSK_STAGES_H
+
+#include "hsk.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Stage S1, 2-bit encoding (Sec. 2.2: reads are encoded before k-mers are
+ * parsed).  d_reads holds n_bases ASCII bytes; d_offsets n_reads + 1 entries.
+ * Outputs (caller-allocated): d_packed ceil(n_bases/32) + 4 words;
+ * d_invalid and d_start ceil(n_bases/64) + 4 words each.  d_invalid marks
+ * bytes other than upper-case A/C/G/T; d_start marks the first base of every
+ * non-empty read.  Words past the data are zero. */
+int hsk_stage_encode(hsk_ctx* ctx, const char* d_reads, uint64_t n_bases,
+                     const uint64_t* d_offsets, uint64_t n_reads, uint64_t* d_packed,
+                     uint64_t* d_invalid, uint64_t* d_start, void* stream);
+
+/* Stage S2, canonical k-mers and hash-scored minimizers (Sec. 3.2).  For
+ * every window start g in [0, n_bases): d_valid[g] = 1 if bases g..g+k-1 are
+ * all ACGT and inside one read, else 0; for valid windows d_key[2g], d_key[2g+1]
+ * = {lo, hi} of the canonical 2k-bit code and d_minhash[g] = the minimum over
+ * the window's k-m+1 m-mers of fmix64(canonical m-mer XOR seed).  Entries of
+ * invalid windows are unspecified.  Outputs caller-allocated: n_bases,
+ * 2*n_bases and n_bases elements. */
+int hsk_stage_windows(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offsets,
+                      uint64_t n_reads, uint64_t n_bases, int k, int m, uint8_t* d_valid,
+                      uint64_t* d_key, uint64_t* d_minhash, void* stream);
+
+/* Stage S3, supermers scattered into minimizer-hashed buckets (Sec. 2.4,
+ * Sec. 3.2; the buckets are the tasks of Sec. 3.4).  A window's bucket is
+ * floor(minhash * n_buckets / 2^64); a supermer is a run of consecutive valid
+ * windows of one read with equal buckets, cut at most every max_kmers windows
+ * (and where the implementation's tiles end).  Outputs: d_bucket_kmers
+ * (caller, n_buckets words) = k-mers per bucket; d_bucket_rec (caller,
+ * n_buckets + 1 words) = first record of each bucket, last entry = total;
+ * *d_records = context-owned device array of *n_records records of
+ * *record_words words, grouped by bucket in ascending bucket order. */
+int hsk_stage_supermers(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offsets,
+                        uint64_t n_reads, uint64_t n_bases, int k, int m, uint32_t n_buckets,
+                        uint64_t* d_bucket_kmers, uint64_t* d_bucket_rec,
+                        const uint64_t** d_records, uint64_t* n_records, int* record_words,
+                        int* max_kmers, void* stream);
+
+/* Stage S4, LSD radix sort of packed keys (Sec. 3.1: equal k-mers become
+ * adjacent).  Sorts n keys of key_words uint64 words (1, or 2 as {lo, hi})
+ * in place, ascending, looking only at the low key_bits bits (1..128); the
+ * other bits must be zero.  Scratch is context-owned. */
+int hsk_stage_sort(hsk_ctx* ctx, uint64_t* d_keys, uint64_t n, int key_words, int key_bits,
+                   void* stream);
+
+/* Stage S5, linear scan of sorted keys (Sec. 3.1): run lengths, histogram
+ * of all runs (as in hsk.h), filter lo <= count <= hi.  d_sorted holds n keys
+ * of key_words words in ascending order.  *out receives context-owned device
+ * arrays; n_windows = n. */
+int hsk_stage_rle(hsk_ctx* ctx, const uint64_t* d_sorted, uint64_t n, int key_words,
+                  uint32_t lo, uint32_t hi, void* stream, hsk_result* out);
+
+/* Stage S6, output order: sort n (key, count) pairs by key, ascending, in
+ * place (keys of key_words words with key_bits significant bits; counts move
+ * with their keys).  Keys must be distinct for the order to be unique. */
+int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t n,
+                    int key_words, int key_bits, void* stream);
+
+/* Test hooks.  hsk_debug_fail_alloc_after(ctx, n): the n-th following device
+ * allocation of the context fails as if the budget were exhausted (-1 turns
+ * this off), to check that every caller returns HSK_ENOMEM cleanly.
+ * hsk_debug_allocated: bytes of device memory the context holds now. */
+int hsk_debug_fail_alloc_after(hsk_ctx* ctx, int n);
+uint64_t hsk_debug_allocated(hsk_ctx* ctx);
+
+/* Profiling hooks.  When enabled, each counting call on the context records
+ * CUDA events on its own stream at the boundaries of its stages and adds the
+ * device time between them to per-stage totals:
+ *   0 S1 encode, 1 S2 k-mers/minimizers + supermer count + bucket scan,
+ *   2 S3 supermer scatter, 3 S4 record expansion + digit histograms,
+ *   4 S4 radix passes, 5 S5 run-length count/filter/histogram, 6 S6 order.
+ * hsk_profile_read copies HSK_N_STAGES totals (ms) and the number of radix-pass
+ * launches they include, then clears them when reset != 0.
+ * hsk_launch_count: kernels launched by this library in this process so far. */
+#define HSK_N_STAGES 7
+int hsk_profile_enable(hsk_ctx* ctx, int on);
+int hsk_profile_read(hsk_ctx* ctx, double* stage_ms, uint64_t* radix_pass_launches, int reset);
+uint64_t hsk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSK_STAGES_H */

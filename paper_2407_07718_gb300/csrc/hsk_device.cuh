@@ -1,0 +1,218 @@
+// hsk_device.cuh -- device helpers shared by the k-mer counting kernels.
+//
+// Key types: k <= 32 uses uint64 (the 2k-bit canonical code, right aligned);
+// 33 <= k <= 64 uses key128 {lo, hi}.  Bases are 2-bit codes A=0 C=1 G=2 T=3,
+// the first base of a k-mer in its most significant bits, so numeric order is
+// lexicographic order of the k-mer string (Sec. 2.1 defines k-mers; the code
+// and the canonical form are this library's reading of it).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "hsk_internal.h"
+
+namespace hsk {
+
+typedef unsigned long long u64;
+
+struct key128 {
+    u64 lo, hi;
+};
+
+__device__ __forceinline__ bool key_lt(u64 a, u64 b) { return a < b; }
+__device__ __forceinline__ bool key_lt(const key128& a, const key128& b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool key_eq(u64 a, u64 b) { return a == b; }
+__device__ __forceinline__ bool key_eq(const key128& a, const key128& b) {
+    return a.hi == b.hi && a.lo == b.lo;
+}
+
+// Radix digit of `bits` bits starting at bit `shift`.
+__device__ __forceinline__ uint32_t key_digit(u64 k, int shift, uint32_t mask) {
+    return (uint32_t)(k >> shift) & mask;
+}
+__device__ __forceinline__ uint32_t key_digit(const key128& k, int shift, uint32_t mask) {
+    if (shift >= 64) return (uint32_t)(k.hi >> (shift - 64)) & mask;
+    u64 v = k.lo >> shift;
+    if (shift > 0) v |= k.hi << (64 - shift);
+    return (uint32_t)v & mask;
+}
+
+// 64 bits of a most-significant-first bit stream starting `off` (0..63) bits
+// into word a (b is the following word).
+__device__ __forceinline__ u64 funnel64(u64 a, u64 b, uint32_t off) {
+    return (a << off) | ((b >> 1) >> (63 - off));
+}
+
+// Reverse the order of 2-bit groups of x (complement applied by the caller).
+__device__ __forceinline__ u64 reverse_pairs(u64 x) {
+    x = __brevll(x);
+    return ((x >> 1) & 0x5555555555555555ULL) | ((x & 0x5555555555555555ULL) << 1);
+}
+
+// Reverse complement of a right-aligned code of k <= 32 bases.
+__device__ __forceinline__ u64 revcomp64(u64 fwd, int k) {
+    return reverse_pairs(~fwd) >> (64 - 2 * k);
+}
+
+// Reverse complement of a right-aligned code of 33 <= k <= 64 bases.
+__device__ __forceinline__ key128 revcomp128(const key128& f, int k) {
+    u64 nh = reverse_pairs(~f.lo), nl = reverse_pairs(~f.hi);  // full 128-bit reversal
+    int s = 128 - 2 * k;                                       // 0 .. 62
+    key128 r;
+    if (s == 0) {
+        r.lo = nl;
+        r.hi = nh;
+    } else {
+        r.lo = (nl >> s) | (nh << (64 - s));
+        r.hi = nh >> s;
+    }
+    return r;
+}
+
+// Code of the k (<= 32) bases starting at base index p of a packed stream.
+__device__ __forceinline__ u64 extract_k64(const u64* w, u64 p, int k) {
+    u64 i = p >> 5;
+    uint32_t off = (uint32_t)(p & 31) * 2;
+    return funnel64(w[i], w[i + 1], off) >> (64 - 2 * k);
+}
+
+// Code of the k (33..64) bases starting at base index p of a packed stream.
+__device__ __forceinline__ key128 extract_k128(const u64* w, u64 p, int k) {
+    u64 i = p >> 5;
+    uint32_t off = (uint32_t)(p & 31) * 2;
+    u64 a = funnel64(w[i], w[i + 1], off);
+    u64 b = funnel64(w[i + 1], w[i + 2], off);
+    int s = 128 - 2 * k;  // 0..62
+    key128 r;
+    if (s == 0) {
+        r.hi = a;
+        r.lo = b;
+    } else {
+        r.hi = a >> s;
+        r.lo = (b >> s) | (a << (64 - s));
+    }
+    return r;
+}
+
+__device__ __forceinline__ u64 canonical64(u64 fwd, int k) {
+    u64 rc = revcomp64(fwd, k);
+    return fwd < rc ? fwd : rc;
+}
+__device__ __forceinline__ key128 canonical128(const key128& fwd, int k) {
+    key128 rc = revcomp128(fwd, k);
+    return key_lt(fwd, rc) ? fwd : rc;
+}
+
+// The n (1..64) mask bits starting at bit p of a most-significant-first mask.
+__device__ __forceinline__ u64 mask_bits(const u64* w, u64 p, int n) {
+    u64 i = p >> 6;
+    uint32_t off = (uint32_t)(p & 63);
+    u64 v = funnel64(w[i], w[i + 1], off);
+    return n >= 64 ? v : (v >> (64 - n));
+}
+
+// MurmurHash3's 64-bit finalizer (A. Appleby, public domain): the m-mer score
+// of Sec. 3.2.
+__device__ __forceinline__ u64 fmix64(u64 h) {
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdULL;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ULL;
+    h ^= h >> 33;
+    return h;
+}
+
+// Bucket (task) of a minimizer score: floor(score * n_buckets / 2^64).
+__device__ __forceinline__ uint32_t bucket_of(u64 score, uint32_t n_buckets) {
+    return (uint32_t)__umul64hi(score, (u64)n_buckets);
+}
+
+// ---------------------------------------------------------------------------
+// device error flag and bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void raise_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(u64* p, u64 v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Look-back status word: [63:62] flag, [61:48] epoch, [47:0] value.
+constexpr u64 LB_AGG = 1ULL << 62;
+constexpr u64 LB_PREFIX = 2ULL << 62;
+constexpr u64 LB_VALUE = (1ULL << 48) - 1;
+__device__ __forceinline__ u64 lb_word(u64 flag, uint32_t epoch, u64 value) {
+    return flag | ((u64)(epoch & 0x3FFF) << 48) | (value & LB_VALUE);
+}
+
+// Decoupled look-back for one value (Merrill & Garland, 2016): sum the values
+// of tiles before `tile` until one carries an inclusive prefix.  Bounded: after
+// LB_SPIN_LIMIT empty reads the wait gives up, raises HSK_DERR_TIMEOUT and
+// returns what it has (the host then discards the result).
+__device__ __forceinline__ u64 lookback_exclusive(u64* status, u64 stride, u64 tile,
+                                                  uint32_t epoch, int* err) {
+    u64 excl = 0;
+    long long j = (long long)tile - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        u64 s = ld_relaxed(status + (u64)j * stride);
+        uint32_t ep = (uint32_t)(s >> 48) & 0x3FFF;
+        u64 fl = s & (3ULL << 62);
+        if (fl == 0 || ep != (epoch & 0x3FFF)) {
+            if (++spins > HSK_SPIN_LIMIT) {
+                raise_error(err, HSK_DERR_TIMEOUT);
+                break;
+            }
+            if (spins > 64) __nanosleep(64);
+            continue;
+        }
+        excl += s & LB_VALUE;
+        if (fl == LB_PREFIX) break;
+        --j;
+    }
+    return excl;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_sum(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+// Exclusive prefix sum over a block of NT threads (NT <= 1024, multiple of
+// 32); `total` receives the block sum.  Uses NT/32 words of `scratch`.
+template <int NT, typename T>
+__device__ __forceinline__ T block_excl_sum(T v, T* scratch, T& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = warp_incl_sum(v);
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < NT / 32 ? scratch[lane] : T(0);
+        T wi = warp_incl_sum(w);
+        if (lane < NT / 32) scratch[lane] = wi - w;
+        if (lane == NT / 32 - 1) scratch[NT / 32] = wi;
+    }
+    __syncthreads();
+    T r = scratch[warp] + inc - v;
+    total = scratch[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace hsk

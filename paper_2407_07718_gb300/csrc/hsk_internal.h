@@ -1,0 +1,102 @@
+// hsk_internal.h -- launch wrappers and parameter blocks shared between the
+// kernel translation units and the host runtime.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+// Device-side error codes written to the context's error word.
+#define HSK_DERR_TIMEOUT 1  // a bounded spin gave up
+#define HSK_DERR_BOUNDS 2   // an index check failed (inconsistent counts)
+#define HSK_DERR_OFFSETS 3  // read offsets are not monotone / do not match n_bases
+
+// Empty reads of a look-back status word before a wait gives up (with a
+// 64 ns back-off after the first 64 reads this bounds a wait to ~1 s).
+#define HSK_SPIN_LIMIT (1u << 24)
+
+namespace hsk {
+
+// Kernels launched by this library (all launch_* wrappers add to it).
+void count_launch(unsigned n = 1);
+
+// ---- S1 encode ----------------------------------------------------------
+void launch_encode(const char* reads, uint64_t n_bases, uint64_t* packed, uint64_t* invalid,
+                   uint64_t n_packed_words, uint64_t n_mask_words, cudaStream_t st);
+void launch_mark_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,
+                        uint64_t* start_mask, int* err, cudaStream_t st);
+
+// ---- S2/S3 canonical k-mers, minimizers, supermers -------------------------
+enum { SM_COUNT = 0, SM_SCATTER = 1, SM_DUMP = 2 };
+
+struct SmParams {
+    const uint64_t* packed;
+    const uint64_t* invalid;
+    const uint64_t* start;
+    uint64_t n_bases;
+    uint64_t n_packed_words, n_mask_words;
+    int k, m, w;
+    uint64_t seed;
+    uint32_t n_buckets;
+    int nmax;          // k-mers per supermer record at most
+    int rec_words;     // 2 (k <= 32) or 4 (k <= 64)
+    uint32_t grid;     // CTAs of the count and scatter launches (must match)
+    uint32_t* cta_counts;     // [n_buckets][grid] records per (bucket, CTA)      (count)
+    uint64_t* bucket_kmers;   // [n_buckets] k-mers per bucket (atomic adds)      (count)
+    const uint64_t* cta_off;  // [n_buckets][grid] first record slot             (scatter)
+    uint64_t* records;        // record array                                     (scatter)
+    uint64_t n_records_cap;
+    uint8_t* dump_valid;      // (dump)
+    uint64_t* dump_key;
+    uint64_t* dump_minhash;
+    int* err;
+};
+
+size_t supermer_smem_bytes(int mode, uint32_t n_buckets);
+int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets);
+void launch_supermer(int mode, const SmParams& p, cudaStream_t st);
+
+// exclusive scan of n uint32 counts into uint64 offsets; offsets[n] = total.
+// Scratch: scan_status_words(n) uint64 words.
+uint64_t scan_status_words(uint64_t n);
+// out[b] = off[b * stride] for b in [0, B]; off[B * stride] is the total
+void launch_gather_stride(const uint64_t* off, uint32_t B, uint32_t stride, uint64_t* out,
+                          cudaStream_t st);
+void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* status,
+                     uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st);
+
+// ---- S4 sort ---------------------------------------------------------------
+// Expand records [0, n_rec) into canonical keys (in record order) and add the
+// per-pass digit histograms of the keys into hist[n_pass][256].
+void launch_expand(const uint64_t* records, uint64_t n_rec, int rec_words, int k, void* keys,
+                   uint64_t n_keys, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch,
+                   uint64_t* hist, int n_pass, int* err, int grid, cudaStream_t st);
+int expand_grid(int num_sms);
+uint64_t expand_status_words(uint64_t n_rec);
+
+// Digit histograms of plain keys (stage sort and pair order).
+void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hist, int n_pass,
+                       int grid, cudaStream_t st);
+// digit_off[p][d] = exclusive prefix over d of hist[p][d]
+void launch_digit_offsets(const uint64_t* hist, uint64_t* digit_off, int n_pass, cudaStream_t st);
+
+// One LSD pass over n keys (optionally carrying uint32 values).
+uint64_t onesweep_tiles(uint64_t n, int key_words);
+void launch_onesweep(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, uint64_t n,
+                     int key_words, int shift, const uint64_t* digit_off, uint64_t* status,
+                     uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st);
+
+// ---- S5 run-length count, filter, histogram -------------------------------
+uint64_t rle_tiles(uint64_t n, int key_words);
+// heads[0..D) = start index of every run; heads[D] = n; *n_heads = D.
+void launch_rle_heads(const void* keys, uint64_t n, int key_words, uint32_t* heads,
+                      uint64_t* n_heads, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch,
+                      int* err, cudaStream_t st);
+// For every run: histogram, max, filter; appends kept (key, count) at out + base.
+void launch_rle_emit(const void* keys, const uint32_t* heads, const uint64_t* n_heads,
+                     uint64_t n_heads_host, int key_words, uint32_t lo, uint32_t hi,
+                     uint64_t* hist, uint32_t hist_len, uint32_t* max_count, void* out_keys,
+                     uint32_t* out_counts, uint64_t* n_out, uint64_t* status, uint32_t* tile_ctr,
+                     uint32_t epoch, int* err, cudaStream_t st);
+
+}  // namespace hsk

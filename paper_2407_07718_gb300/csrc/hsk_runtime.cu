@@ -1,0 +1,896 @@
+// hsk_runtime.cu -- host runtime and C ABI of the k-mer counter.
+//
+// The context owns a device arena (named buffers grown on demand, all counted
+// against an HBM budget), a stream, a device error word and the look-back
+// bookkeeping (epoch-tagged status words, tile counters).  hsk_count_device
+// runs the whole pipeline on one stream:
+//
+//   S1 encode -> S2/S3 count supermers per (bucket, CTA) -> scan -> plan
+//   chunks of buckets under the budget -> S3 scatter records -> per chunk:
+//   S4 expand records to keys (+ digit histograms), 8-bit LSD passes ->
+//   S5 run heads, counts, histogram, filter -> S6 order pairs when the job
+//   took more than one chunk.
+//
+// Buckets are the paper's tasks (Sec. 3.4): a k-mer value never lands in two
+// of them, so chunks of buckets are sorted and counted independently, the way
+// the paper's workers count tasks.  The chunk planner plays the role of the
+// paper's memory-aware choice between an out-of-place and an in-place sort
+// (Sec. 3.1): it sizes each chunk so the out-of-place sort fits the budget.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hsk.h"
+#include "../../include/hsk_stages.h"
+#include "hsk_internal.h"
+#include "hsk_runtime.h"
+
+using namespace hsk;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+void hsk_set_error(hsk_ctx* c, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err_msg = buf;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            hsk_set_error(c, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
+                          __FILE__, __LINE__);                                              \
+            return HSK_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)
+
+#define TRY(x)                      \
+    do {                            \
+        int rc_ = (x);              \
+        if (rc_ != HSK_OK) return rc_; \
+    } while (0)
+
+int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new) {
+    if (bytes == 0) bytes = 256;
+    if (b.cap >= bytes) return HSK_OK;
+    size_t want = (bytes + (2u << 20) - 1) & ~size_t((2u << 20) - 1);  // 2 MiB granules
+    if (c->allocated - b.cap + want > c->budget) {
+        hsk_set_error(c, "device memory budget exceeded: need %zu more bytes, budget %zu, held %zu",
+                      want - b.cap, c->budget, c->allocated);
+        return HSK_ENOMEM;
+    }
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess) {
+            hsk_set_error(c, "cudaFree: %s", cudaGetErrorString(e));
+            return HSK_ECUDA;
+        }
+        c->allocated -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    if (c->fail_alloc_after >= 0 && c->fail_alloc_after-- == 0) {
+        hsk_set_error(c, "injected allocation failure");
+        return HSK_ENOMEM;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hsk_set_error(c, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+        b.p = nullptr;
+        return HSK_ENOMEM;
+    }
+    b.cap = want;
+    c->allocated += want;
+    if (zero_new) {  // ordered before every later kernel on the call's stream
+        e = cudaMemsetAsync(b.p, 0, want, c->zst);
+        if (e != cudaSuccess) {
+            hsk_set_error(c, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+            return HSK_ECUDA;
+        }
+    }
+    return HSK_OK;
+}
+
+static void free_buf(hsk_ctx* c, DevBuf& b) {
+    if (b.p) {
+        cudaFree(b.p);
+        c->allocated -= b.cap;
+    }
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+// A fresh epoch for a look-back launch (status words of other launches never
+// match).  Epochs run 1..16383; on wrap-around the status buffer is cleared.
+int hsk_next_epoch(hsk_ctx* c, cudaStream_t st, uint32_t* epoch) {
+    if (++c->epoch > 0x3FFF) {
+        c->epoch = 1;
+        if (c->lb_status.p) CK(cudaMemsetAsync(c->lb_status.p, 0, c->lb_status.cap, st));
+    }
+    *epoch = c->epoch;
+    return HSK_OK;
+}
+
+// A zeroed tile counter for a look-back launch.
+int hsk_next_counter(hsk_ctx* c, cudaStream_t st, uint32_t** ctr) {
+    if (c->ctr_used >= HSK_N_COUNTERS) {
+        CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+        c->ctr_used = 0;
+    }
+    *ctr = c->counters + c->ctr_used++;
+    return HSK_OK;
+}
+
+// Grow the shared look-back status buffer (new memory is zeroed: stale bytes
+// could otherwise look like a status word of the current epoch).
+static int ensure_status(hsk_ctx* c, uint64_t words, cudaStream_t st) {
+    if (c->lb_status.cap >= words * 8) return HSK_OK;
+    CK(cudaStreamSynchronize(st));
+    return hsk_ensure(c, c->lb_status, words * 8, true);
+}
+
+extern "C" int hsk_config_default(hsk_config* cfg) {
+    if (!cfg) return HSK_EINVAL;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->device = 0;
+    cfg->hbm_budget = 0;
+    cfg->hist_len = 65536;
+    cfg->n_buckets = 0;
+    cfg->radix_bits = 8;
+    cfg->max_chunk_kmers = 0;
+    cfg->seed = 0x9E3779B97F4A7C15ULL;
+    cfg->autotune = 1;
+    return HSK_OK;
+}
+
+extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
+    if (!out) return HSK_EINVAL;
+    *out = nullptr;
+    hsk_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else hsk_config_default(&cfg);
+    if (cfg.hist_len < 2 || (cfg.radix_bits != 0 && cfg.radix_bits != 8)) return HSK_EINVAL;
+    hsk_ctx* c = new hsk_ctx();
+    c->cfg = cfg;
+    cudaError_t e = cudaSetDevice(cfg.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg.device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    size_t free_b = 0, total_b = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    if (e == cudaSuccess) e = cudaMalloc(&c->small, HSK_SMALL_BYTES);
+    if (e == cudaSuccess) e = cudaMemset(c->small, 0, HSK_SMALL_BYTES);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return HSK_ECUDA;
+    }
+    c->budget = cfg.hbm_budget ? cfg.hbm_budget : (size_t)(free_b * 0.9);
+    c->allocated = HSK_SMALL_BYTES;
+    char* s = (char*)c->small;
+    c->d_err = (int*)(s + 0);
+    c->d_max = (uint32_t*)(s + 8);
+    c->d_nheads = (uint64_t*)(s + 16);
+    c->d_nout = (uint64_t*)(s + 24);
+    c->counters = (uint32_t*)(s + 256);
+    *out = c;
+    return HSK_OK;
+}
+
+extern "C" void hsk_destroy(hsk_ctx* c) {
+    if (!c) return;
+    hsk_serve_shutdown(c);
+    cudaSetDevice(c->cfg.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (DevBuf* b : c->all_bufs()) free_buf(c, *b);
+    if (c->small) cudaFree(c->small);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    delete c;
+}
+
+extern "C" const char* hsk_last_error(hsk_ctx* c) { return c ? c->err_msg.c_str() : "null context"; }
+
+// test hook: make the n-th following device allocation fail (-1 = never)
+extern "C" int hsk_debug_fail_alloc_after(hsk_ctx* c, int n) {
+    if (!c) return HSK_EINVAL;
+    c->fail_alloc_after = n;
+    return HSK_OK;
+}
+
+extern "C" uint64_t hsk_debug_allocated(hsk_ctx* c) { return c ? c->allocated : 0; }
+
+// ---------------------------------------------------------------------------
+// launch counter and stage profiling
+// ---------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+namespace hsk {
+void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace hsk
+
+extern "C" uint64_t hsk_launch_count(void) { return g_launches.load(); }
+
+static void prof_mark(hsk_ctx* c, cudaStream_t st, int stage) {
+    if (!c->prof) return;
+    size_t i = c->marks.size();
+    if (i >= c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->ev_pool.push_back(e);
+    }
+    cudaEventRecord(c->ev_pool[i], st);
+    c->marks.emplace_back((int)i, stage);
+}
+
+// after the stream is synchronized: add the spans between marks to their stages
+static void prof_collect(hsk_ctx* c) {
+    if (!c->prof) return;
+    for (size_t i = 1; i < c->marks.size(); ++i) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[c->marks[i - 1].first], c->ev_pool[c->marks[i].first]) ==
+                cudaSuccess &&
+            c->marks[i].second >= 0)
+            c->prof_ms[c->marks[i].second] += ms;
+    }
+    c->marks.clear();
+}
+
+extern "C" int hsk_profile_enable(hsk_ctx* c, int on) {
+    if (!c) return HSK_EINVAL;
+    c->prof = on != 0;
+    c->marks.clear();
+    return HSK_OK;
+}
+
+extern "C" int hsk_profile_read(hsk_ctx* c, double* stage_ms, uint64_t* passes, int reset) {
+    if (!c) return HSK_EINVAL;
+    for (int i = 0; i < HSK_N_STAGES; ++i) {
+        if (stage_ms) stage_ms[i] = c->prof_ms[i];
+        if (reset) c->prof_ms[i] = 0;
+    }
+    if (passes) *passes = c->prof_passes;
+    if (reset) c->prof_passes = 0;
+    return HSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+static int check_args(hsk_ctx* c, const void* reads, const void* offsets, uint64_t n_reads, int k,
+                      int m, uint32_t lo, uint32_t hi) {
+    if (!c) return HSK_EINVAL;
+    if (k < 1 || k > 64) {
+        hsk_set_error(c, "k=%d outside [1, 64]", k);
+        return HSK_EINVAL;
+    }
+    if (m < 1 || m > k || m > 32) {
+        hsk_set_error(c, "m=%d outside [1, min(k, 32)]", m);
+        return HSK_EINVAL;
+    }
+    if (lo > hi) {
+        hsk_set_error(c, "filter bounds lo=%u > hi=%u", lo, hi);
+        return HSK_EINVAL;
+    }
+    if (n_reads > 0 && (!reads && !offsets)) {
+        hsk_set_error(c, "NULL reads/offsets with n_reads=%llu", (unsigned long long)n_reads);
+        return HSK_EINVAL;
+    }
+    if (n_reads > 0 && !offsets) {
+        hsk_set_error(c, "NULL offsets with n_reads=%llu", (unsigned long long)n_reads);
+        return HSK_EINVAL;
+    }
+    return HSK_OK;
+}
+
+static int read_device_error(hsk_ctx* c, cudaStream_t st) {
+    int derr = 0;
+    CK(cudaMemcpyAsync(&derr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (derr == HSK_DERR_OFFSETS) {
+        hsk_set_error(c, "offsets must start at 0, be non-decreasing and end at n_bases");
+        return HSK_EINVAL;
+    }
+    if (derr == HSK_DERR_TIMEOUT) {
+        hsk_set_error(c, "a bounded device wait gave up (look-back status never arrived)");
+        return HSK_ETIMEOUT;
+    }
+    if (derr != 0) {
+        hsk_set_error(c, "device consistency check failed (code %d)", derr);
+        return HSK_ECUDA;
+    }
+    return HSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pipeline pieces
+// ---------------------------------------------------------------------------
+int hsk_encode_into(hsk_ctx* c, const char* d_reads, uint64_t n_bases, const uint64_t* d_offsets,
+                    uint64_t n_reads, DevBuf& pk, DevBuf& iv, DevBuf& rs, Encoded& E,
+                    cudaStream_t st) {
+    E.n_bases = n_bases;
+    E.n_pw = (n_bases + 31) / 32;
+    E.n_mw = (n_bases + 63) / 64;
+    TRY(hsk_ensure(c, pk, (E.n_pw + 8) * 8, false));
+    TRY(hsk_ensure(c, iv, (E.n_mw + 8) * 8, false));
+    TRY(hsk_ensure(c, rs, (E.n_mw + 8) * 8, false));
+    CK(cudaMemsetAsync((uint64_t*)pk.p + E.n_pw, 0, 8 * 8, st));
+    CK(cudaMemsetAsync((uint64_t*)iv.p + E.n_mw, 0, 8 * 8, st));
+    CK(cudaMemsetAsync(rs.p, 0, (E.n_mw + 8) * 8, st));
+    launch_mark_starts(d_offsets, n_reads, n_bases, (uint64_t*)rs.p, c->d_err, st);
+    launch_encode(d_reads, n_bases, (uint64_t*)pk.p, (uint64_t*)iv.p, E.n_pw, E.n_mw, st);
+    CK(cudaGetLastError());
+    E.packed = (const uint64_t*)pk.p;
+    E.invalid = (const uint64_t*)iv.p;
+    E.start = (const uint64_t*)rs.p;
+    return HSK_OK;
+}
+
+uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases) {
+    if (c->cfg.n_buckets) return c->cfg.n_buckets;
+    // small jobs: fewer buckets keep the per-CTA tables cheap
+    if (n_bases < (1ull << 22)) return 256;
+    return 4096;
+}
+
+static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, SmParams& P) {
+    memset(&P, 0, sizeof(P));
+    P.packed = E.packed;
+    P.invalid = E.invalid;
+    P.start = E.start;
+    P.n_bases = E.n_bases;
+    P.n_packed_words = E.n_pw;
+    P.n_mask_words = E.n_mw;
+    P.k = k;
+    P.m = m;
+    P.w = k - m + 1;
+    P.seed = c->cfg.seed;
+    P.n_buckets = B;
+    P.rec_words = k <= 32 ? 2 : 4;
+    P.nmax = (P.rec_words * 32 - 4) - k + 1;  // bases per record minus (k - 1)
+    if (P.nmax > 255) P.nmax = 255;
+    P.err = c->d_err;
+}
+
+// Count supermers per (bucket, CTA), scan to record offsets, scatter records.
+int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S,
+                  cudaStream_t st) {
+    SmParams P;
+    fill_sm_params(c, E, k, m, B, P);
+    const bool wide = k > 32;
+    const int nreg = P.w <= 33 ? 2 : 3;
+    int occ = std::min(supermer_max_ctas_per_sm(SM_SCATTER, wide, nreg, B),
+                       supermer_max_ctas_per_sm(SM_COUNT, wide, nreg, B));
+    uint64_t warp_tiles = (E.n_bases + 1023) / 1024;
+    uint64_t g = std::min<uint64_t>((uint64_t)c->num_sms * occ, (warp_tiles + 7) / 8);
+    if (g == 0) g = 1;
+    P.grid = (uint32_t)g;
+    uint64_t nc = (uint64_t)B * g;
+    TRY(hsk_ensure(c, c->cta_cnt, nc * 4, false));
+    TRY(hsk_ensure(c, c->cta_off, (nc + 1) * 8, false));
+    TRY(hsk_ensure(c, c->bucket_kmers, (uint64_t)B * 8, false));
+    TRY(hsk_ensure(c, c->bucket_rec, ((uint64_t)B + 1) * 8, false));
+    CK(cudaMemsetAsync(c->bucket_kmers.p, 0, (size_t)B * 8, st));
+    CK(cudaMemsetAsync(c->cta_cnt.p, 0, nc * 4, st));  // stays zero when there is no base
+    P.cta_counts = (uint32_t*)c->cta_cnt.p;
+    P.bucket_kmers = (uint64_t*)c->bucket_kmers.p;
+    launch_supermer(SM_COUNT, P, st);
+    CK(cudaGetLastError());
+    // exclusive scan over (bucket-major, CTA-minor) counts
+    TRY(ensure_status(c, scan_status_words(nc), st));
+    uint32_t ep, *ctr;
+    TRY(hsk_next_epoch(c, st, &ep));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_scan_u32((const uint32_t*)c->cta_cnt.p, nc, (uint64_t*)c->cta_off.p,
+                    (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    launch_gather_stride((const uint64_t*)c->cta_off.p, B, (uint32_t)g, (uint64_t*)c->bucket_rec.p, st);
+    CK(cudaGetLastError());
+    // bucket statistics to the host (needed to size records and plan chunks)
+    S.B = B;
+    S.h_bucket_kmers.resize(B);
+    S.h_bucket_rec.resize((size_t)B + 1);
+    CK(cudaMemcpyAsync(S.h_bucket_kmers.data(), c->bucket_kmers.p, (size_t)B * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(S.h_bucket_rec.data(), c->bucket_rec.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, st));
+    TRY(read_device_error(c, st));
+    S.n_records = S.h_bucket_rec[B];
+    S.n_kmers = 0;
+    for (uint64_t v : S.h_bucket_kmers) S.n_kmers += v;
+    S.rec_words = P.rec_words;
+    S.nmax = P.nmax;
+    TRY(hsk_ensure(c, c->records, std::max<uint64_t>(S.n_records, 1) * P.rec_words * 8, false));
+    prof_mark(c, st, 1);
+    P.cta_off = (const uint64_t*)c->cta_off.p;
+    P.records = (uint64_t*)c->records.p;
+    P.n_records_cap = S.n_records;
+    launch_supermer(SM_SCATTER, P, st);
+    CK(cudaGetLastError());
+    S.records = (const uint64_t*)c->records.p;
+    return HSK_OK;
+}
+
+static int n_passes_for(int key_bits) { return (key_bits + 7) / 8; }
+
+// LSD sort of n keys in a (b is scratch of the same size); *sorted_in_b tells
+// where the result ended.  hist[n_pass][256] must hold the digit histograms.
+int hsk_sort_passes(hsk_ctx* c, void* a, void* b, uint32_t* va, uint32_t* vb, uint64_t n,
+                    int key_words, int n_pass, uint64_t* hist, bool* sorted_in_b, cudaStream_t st,
+                    bool make_offsets = true) {
+    *sorted_in_b = false;
+    if (n == 0 || n_pass == 0) return HSK_OK;
+    TRY(ensure_status(c, onesweep_tiles(n, key_words) * 256 + 1, st));
+    if (make_offsets) launch_digit_offsets(hist, (uint64_t*)c->digit_off.p, n_pass, st);
+    void *src = a, *dst = b;
+    uint32_t *vs = va, *vd = vb;
+    for (int p = 0; p < n_pass; ++p) {
+        uint32_t ep, *ctr;
+        TRY(hsk_next_epoch(c, st, &ep));
+        TRY(hsk_next_counter(c, st, &ctr));
+        launch_onesweep(src, dst, vs, vd, n, key_words, 8 * p, (uint64_t*)c->digit_off.p + 256 * p,
+                        (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+        std::swap(src, dst);
+        std::swap(vs, vd);
+    }
+    CK(cudaGetLastError());
+    *sorted_in_b = (n_pass % 2) == 1;
+    return HSK_OK;
+}
+
+// Heads + emit for one sorted chunk; appends to the context's pair output.
+int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uint32_t lo,
+                  uint32_t hi, uint32_t hist_len, uint64_t* d_hist, Output& O, cudaStream_t st) {
+    if (n == 0) return HSK_OK;
+    if (n >= 0xFFFFFFFFull) {
+        hsk_set_error(c, "a sort chunk of %llu keys exceeds 2^32-1", (unsigned long long)n);
+        return HSK_EOVERFLOW;
+    }
+    TRY(hsk_ensure(c, c->heads, (n + 1) * 4, false));
+    TRY(ensure_status(c, rle_tiles(n, key_words) + 1, st));
+    uint32_t ep, *ctr;
+    TRY(hsk_next_epoch(c, st, &ep));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_rle_heads(sorted, n, key_words, (uint32_t*)c->heads.p, c->d_nheads,
+                     (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    CK(cudaGetLastError());
+    uint64_t D = 0;
+    CK(cudaMemcpyAsync(&D, c->d_nheads, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    O.n_distinct += D;
+    // output capacity: previous pairs + at most D new ones (grown with copy)
+    size_t kb = (size_t)key_words * 8;
+    uint64_t need = O.n_pairs + D;
+    if (c->out_keys.cap < need * kb || c->out_counts.cap < need * 4) {
+        DevBuf nk, ncn;
+        TRY(hsk_ensure(c, nk, need * kb, false));
+        TRY(hsk_ensure(c, ncn, need * 4, false));
+        if (O.n_pairs) {
+            CK(cudaMemcpyAsync(nk.p, c->out_keys.p, O.n_pairs * kb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(ncn.p, c->out_counts.p, O.n_pairs * 4, cudaMemcpyDeviceToDevice, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        free_buf(c, c->out_keys);
+        free_buf(c, c->out_counts);
+        c->out_keys = nk;
+        c->out_counts = ncn;
+    }
+    TRY(ensure_status(c, rle_tiles(D, key_words) + 1, st));
+    TRY(hsk_next_epoch(c, st, &ep));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_rle_emit(sorted, (const uint32_t*)c->heads.p, c->d_nheads, D, key_words, lo, hi, d_hist,
+                    hist_len, c->d_max, (char*)c->out_keys.p + O.n_pairs * kb,
+                    (uint32_t*)c->out_counts.p + O.n_pairs, c->d_nout, (uint64_t*)c->lb_status.p,
+                    ctr, ep, c->d_err, st);
+    CK(cudaGetLastError());
+    uint64_t kept = 0;
+    CK(cudaMemcpyAsync(&kept, c->d_nout, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    O.n_pairs += kept;
+    return HSK_OK;
+}
+
+// Order the output pairs by key (stage S6), needed only for multi-chunk jobs.
+int hsk_order_pairs(hsk_ctx* c, void* keys, uint32_t* counts, uint64_t n, int key_words,
+                    int key_bits, cudaStream_t st) {
+    if (n <= 1) return HSK_OK;
+    size_t kb = (size_t)key_words * 8;
+    int P = n_passes_for(key_bits);
+    TRY(hsk_ensure(c, c->pair_alt_keys, n * kb, false));
+    TRY(hsk_ensure(c, c->pair_alt_counts, n * 4, false));
+    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
+    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
+    CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
+    launch_digit_hist(keys, key_words, n, (uint64_t*)c->pass_hist.p, P, c->num_sms * 4, st);
+    bool in_b = false;
+    TRY(hsk_sort_passes(c, keys, c->pair_alt_keys.p, counts, (uint32_t*)c->pair_alt_counts.p, n,
+                        key_words, P, (uint64_t*)c->pass_hist.p, &in_b, st));
+    if (in_b) {
+        CK(cudaMemcpyAsync(keys, c->pair_alt_keys.p, n * kb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(counts, c->pair_alt_counts.p, n * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    return HSK_OK;
+}
+
+// Plan chunks of consecutive buckets whose keys fit the sort budget.
+int hsk_plan_chunks(hsk_ctx* c, const Supermers& S, int key_words,
+                    std::vector<std::pair<uint32_t, uint32_t>>& chunks) {
+    chunks.clear();
+    size_t kb = (size_t)key_words * 8;
+    // per key: keys + alt keys + heads + look-back status + worst-case output pair
+    double per_key = 2.0 * kb + 4 + (key_words == 1 ? 0.5 : 1.0) + kb + 4;
+    size_t held_sort = c->keys.cap + c->alt.cap + c->heads.cap + c->lb_status.cap + c->out_keys.cap +
+                       c->out_counts.cap;
+    size_t other = c->allocated - held_sort;
+    size_t avail = c->budget > other + (64u << 20) ? c->budget - other - (64u << 20) : 0;
+    uint64_t cap = (uint64_t)(avail / per_key);
+    if (cap > 0xF0000000ull) cap = 0xF0000000ull;  // run heads are 32-bit indices
+    if (c->cfg.max_chunk_kmers && cap > c->cfg.max_chunk_kmers) cap = c->cfg.max_chunk_kmers;
+    uint32_t b0 = 0;
+    uint64_t acc = 0;
+    for (uint32_t b = 0; b < S.B; ++b) {
+        uint64_t v = S.h_bucket_kmers[b];
+        if (v > cap) {
+            hsk_set_error(c, "bucket %u holds %llu k-mers, more than a sort chunk can hold (%llu)", b,
+                          (unsigned long long)v, (unsigned long long)cap);
+            return HSK_ENOMEM;
+        }
+        if (acc + v > cap && b > b0) {
+            chunks.emplace_back(b0, b);
+            b0 = b;
+            acc = 0;
+        }
+        acc += v;
+    }
+    if (S.B > b0) chunks.emplace_back(b0, S.B);
+    return HSK_OK;
+}
+
+int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
+                  uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
+                  DevResult& R) {
+    memset(&R, 0, sizeof(R));
+    c->zst = st;
+    const int kw = k <= 32 ? 1 : 2;
+    const size_t kb = (size_t)kw * 8;
+    const uint32_t H = c->cfg.hist_len;
+    TRY(hsk_ensure(c, c->hist, (size_t)H * 8, false));
+    CK(cudaEventRecord(c->ev0, st));
+    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)H * 8, st));
+    CK(cudaMemsetAsync(c->small, 0, 64, st));  // err, max, n_heads, n_out
+    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+    c->ctr_used = 0;
+    c->marks.clear();
+    prof_mark(c, st, -1);
+    Output O;
+    Encoded E;
+    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
+    prof_mark(c, st, 0);
+    Supermers S;
+    uint32_t B = hsk_pick_buckets(c, n_bases);
+    TRY(hsk_supermers(c, E, k, m, B, S, st));
+    prof_mark(c, st, 2);
+    R.n_windows = S.n_kmers;
+    R.n_supermers = S.n_records;
+    std::vector<std::pair<uint32_t, uint32_t>> chunks;
+    if (S.n_kmers > 0) TRY(hsk_plan_chunks(c, S, kw, chunks));
+    const int P = n_passes_for(2 * k);
+    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
+    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
+    for (auto& ch : chunks) {
+        uint64_t r0 = S.h_bucket_rec[ch.first], r1 = S.h_bucket_rec[ch.second];
+        uint64_t nk = 0;
+        for (uint32_t b = ch.first; b < ch.second; ++b) nk += S.h_bucket_kmers[b];
+        if (nk == 0) continue;
+        TRY(hsk_ensure(c, c->keys, nk * kb, false));
+        TRY(hsk_ensure(c, c->alt, nk * kb, false));
+        TRY(ensure_status(c, expand_status_words(r1 - r0), st));
+        CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
+        uint32_t ep, *ctr;
+        TRY(hsk_next_epoch(c, st, &ep));
+        TRY(hsk_next_counter(c, st, &ctr));
+        launch_expand(S.records + r0 * S.rec_words, r1 - r0, S.rec_words, k, c->keys.p, nk,
+                      (uint64_t*)c->lb_status.p, ctr, ep, (uint64_t*)c->pass_hist.p, P, c->d_err,
+                      expand_grid(c->num_sms), st);
+        CK(cudaGetLastError());
+        launch_digit_offsets((uint64_t*)c->pass_hist.p, (uint64_t*)c->digit_off.p, P, st);
+        prof_mark(c, st, 3);
+        bool in_b = false;
+        TRY(hsk_sort_passes(c, c->keys.p, c->alt.p, nullptr, nullptr, nk, kw, P,
+                            (uint64_t*)c->pass_hist.p, &in_b, st, false));
+        if (c->prof) c->prof_passes += P;
+        prof_mark(c, st, 4);
+        const void* sorted = in_b ? c->alt.p : c->keys.p;
+        TRY(hsk_rle_chunk(c, sorted, nk, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
+        prof_mark(c, st, 5);
+    }
+    if (chunks.size() > 1)
+        TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st));
+    prof_mark(c, st, 6);
+    CK(cudaEventRecord(c->ev1, st));
+    TRY(read_device_error(c, st));
+    prof_collect(c);
+    uint32_t mx = 0;
+    CK(cudaMemcpy(&mx, c->d_max, 4, cudaMemcpyDeviceToHost));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    R.n_pairs = O.n_pairs;
+    R.n_distinct = O.n_distinct;
+    R.max_count = mx;
+    R.n_chunks = (uint32_t)chunks.size();
+    R.key_words = kw;
+    R.kmers = (const uint64_t*)c->out_keys.p;
+    R.counts = (const uint32_t*)c->out_counts.p;
+    R.hist = (const uint64_t*)c->hist.p;
+    R.hist_len = H;
+    R.device_ms = ms;
+    return HSK_OK;
+}
+
+static void to_public(const DevResult& R, hsk_result* out) {
+    memset(out, 0, sizeof(*out));
+    out->n_pairs = R.n_pairs;
+    out->kmers = R.kmers;
+    out->counts = R.counts;
+    out->hist = R.hist;
+    out->hist_len = R.hist_len;
+    out->key_words = R.key_words;
+    out->n_windows = R.n_windows;
+    out->n_distinct = R.n_distinct;
+    out->max_count = R.max_count;
+    out->n_chunks = R.n_chunks;
+    out->n_supermers = R.n_supermers;
+    out->device_ms = R.device_ms;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: plain counting
+// ---------------------------------------------------------------------------
+extern "C" int hsk_count_device(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets,
+                                uint64_t n_reads, uint64_t n_bases, int k, int m, uint32_t lo,
+                                uint32_t hi, void* stream, hsk_result* out) {
+    TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, lo, hi));
+    if (!out) return HSK_EINVAL;
+    if (n_bases > 0 && !d_reads) {
+        hsk_set_error(c, "NULL reads with n_bases > 0");
+        return HSK_EINVAL;
+    }
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    DevResult R;
+    int rc = hsk_run_count(c, d_reads, d_offsets, n_reads, n_bases, k, m, lo, hi, st, R);
+    if (rc != HSK_OK) return rc;
+    to_public(R, out);
+    return HSK_OK;
+}
+
+// Stage host buffers into context device memory, count, copy results back.
+int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, uint64_t n_reads,
+                      int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st, DevBuf& d_reads,
+                      DevBuf& d_offsets, HostResult& HR) {
+    uint64_t n_bases = 0;
+    if (n_reads > 0) {
+        if (offsets[0] != 0) {
+            hsk_set_error(c, "offsets[0] must be 0");
+            return HSK_EINVAL;
+        }
+        for (uint64_t i = 0; i < n_reads; ++i)
+            if (offsets[i + 1] < offsets[i]) {
+                hsk_set_error(c, "offsets not monotone at read %llu", (unsigned long long)i);
+                return HSK_EINVAL;
+            }
+        n_bases = offsets[n_reads];
+        if (n_bases > 0 && !reads) {
+            hsk_set_error(c, "NULL reads with bases present");
+            return HSK_EINVAL;
+        }
+    }
+    TRY(hsk_ensure(c, d_reads, n_bases + 16, false));
+    TRY(hsk_ensure(c, d_offsets, (n_reads + 1) * 8, false));
+    if (n_bases) CK(cudaMemcpyAsync(d_reads.p, reads, n_bases, cudaMemcpyHostToDevice, st));
+    if (n_reads) CK(cudaMemcpyAsync(d_offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(d_offsets.p, 0, 8, st));
+    DevResult R;
+    TRY(hsk_run_count(c, (const char*)d_reads.p, (const uint64_t*)d_offsets.p, n_reads, n_bases, k,
+                      m, lo, hi, st, R));
+    size_t kb = (size_t)R.key_words * 8;
+    HR.kmers.resize(R.n_pairs * R.key_words);
+    HR.counts.resize(R.n_pairs);
+    HR.hist.resize(R.hist_len);
+    if (R.n_pairs) {
+        CK(cudaMemcpyAsync(HR.kmers.data(), R.kmers, R.n_pairs * kb, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(HR.counts.data(), R.counts, R.n_pairs * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(HR.hist.data(), R.hist, (size_t)R.hist_len * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    HR.R = R;
+    HR.R.kmers = HR.kmers.data();
+    HR.R.counts = HR.counts.data();
+    HR.R.hist = HR.hist.data();
+    return HSK_OK;
+}
+
+extern "C" int hsk_count(hsk_ctx* c, const char* reads, const uint64_t* offsets, uint64_t n_reads,
+                         int k, int m, uint32_t lo, uint32_t hi, hsk_result* out) {
+    TRY(check_args(c, reads, offsets, n_reads, k, m, lo, hi));
+    if (!out) return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    TRY(hsk_count_host_on(c, reads, offsets, n_reads, k, m, lo, hi, c->stream, c->in_reads,
+                          c->in_offsets, c->host_res));
+    to_public(c->host_res.R, out);
+    return HSK_OK;
+}
+
+extern "C" int hsk_result_copy(hsk_ctx* c, const hsk_result* r, uint64_t* kmers_dst,
+                               uint32_t* counts_dst, uint64_t* hist_dst, int dst_on_device,
+                               void* stream) {
+    if (!c || !r) return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t kb = (size_t)r->key_words * 8;
+    if (kmers_dst && r->n_pairs)
+        CK(cudaMemcpyAsync(kmers_dst, r->kmers, r->n_pairs * kb, cudaMemcpyDefault, st));
+    if (counts_dst && r->n_pairs)
+        CK(cudaMemcpyAsync(counts_dst, r->counts, r->n_pairs * 4, cudaMemcpyDefault, st));
+    if (hist_dst && r->hist_len)
+        CK(cudaMemcpyAsync(hist_dst, r->hist, (size_t)r->hist_len * 8, cudaMemcpyDefault, st));
+    (void)dst_on_device;  // unified addressing: the runtime infers the direction
+    CK(cudaStreamSynchronize(st));
+    return HSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: stages
+// ---------------------------------------------------------------------------
+extern "C" int hsk_stage_encode(hsk_ctx* c, const char* d_reads, uint64_t n_bases,
+                                const uint64_t* d_offsets, uint64_t n_reads, uint64_t* d_packed,
+                                uint64_t* d_invalid, uint64_t* d_start, void* stream) {
+    if (!c || !d_packed || !d_invalid || !d_start) return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    c->zst = st;
+    uint64_t n_pw = (n_bases + 31) / 32, n_mw = (n_bases + 63) / 64;
+    CK(cudaMemsetAsync(c->small, 0, 64, st));
+    CK(cudaMemsetAsync(d_packed, 0, (n_pw + 4) * 8, st));
+    CK(cudaMemsetAsync(d_invalid, 0, (n_mw + 4) * 8, st));
+    CK(cudaMemsetAsync(d_start, 0, (n_mw + 4) * 8, st));
+    launch_mark_starts(d_offsets, n_reads, n_bases, d_start, c->d_err, st);
+    launch_encode(d_reads, n_bases, d_packed, d_invalid, n_pw, n_mw, st);
+    CK(cudaGetLastError());
+    return read_device_error(c, st);
+}
+
+extern "C" int hsk_stage_windows(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets,
+                                 uint64_t n_reads, uint64_t n_bases, int k, int m, uint8_t* d_valid,
+                                 uint64_t* d_key, uint64_t* d_minhash, void* stream) {
+    TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    c->zst = st;
+    CK(cudaMemsetAsync(c->small, 0, 64, st));
+    Encoded E;
+    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
+    SmParams P;
+    fill_sm_params(c, E, k, m, 1, P);
+    uint64_t warp_tiles = (n_bases + 1023) / 1024;
+    P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->num_sms * 4, (warp_tiles + 7) / 8));
+    P.dump_valid = d_valid;
+    P.dump_key = d_key;
+    P.dump_minhash = d_minhash;
+    launch_supermer(SM_DUMP, P, st);
+    CK(cudaGetLastError());
+    return read_device_error(c, st);
+}
+
+extern "C" int hsk_stage_supermers(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets,
+                                   uint64_t n_reads, uint64_t n_bases, int k, int m,
+                                   uint32_t n_buckets, uint64_t* d_bucket_kmers,
+                                   uint64_t* d_bucket_rec, const uint64_t** d_records,
+                                   uint64_t* n_records, int* record_words, int* max_kmers,
+                                   void* stream) {
+    TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
+    if (n_buckets < 1 || n_buckets > HSK_MAX_BUCKETS || !d_bucket_kmers || !d_bucket_rec || !d_records ||
+        !n_records || !record_words)
+        return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    c->zst = st;
+    CK(cudaMemsetAsync(c->small, 0, 64, st));
+    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+    c->ctr_used = 0;
+    Encoded E;
+    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
+    Supermers S;
+    TRY(hsk_supermers(c, E, k, m, n_buckets, S, st));
+    CK(cudaMemcpyAsync(d_bucket_kmers, c->bucket_kmers.p, (size_t)n_buckets * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d_bucket_rec, c->bucket_rec.p, ((size_t)n_buckets + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    *d_records = S.records;
+    *n_records = S.n_records;
+    *record_words = S.rec_words;
+    if (max_kmers) *max_kmers = S.nmax;
+    return read_device_error(c, st);
+}
+
+extern "C" int hsk_stage_sort(hsk_ctx* c, uint64_t* d_keys, uint64_t n, int key_words, int key_bits,
+                              void* stream) {
+    if (!c || (n && !d_keys) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
+        key_bits > 64 * key_words)
+        return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    c->zst = st;
+    CK(cudaMemsetAsync(c->small, 0, 64, st));
+    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+    c->ctr_used = 0;
+    if (n <= 1) return HSK_OK;
+    size_t kb = (size_t)key_words * 8;
+    int P = n_passes_for(key_bits);
+    TRY(hsk_ensure(c, c->alt, n * kb, false));
+    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
+    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
+    CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
+    launch_digit_hist(d_keys, key_words, n, (uint64_t*)c->pass_hist.p, P, c->num_sms * 4, st);
+    bool in_b = false;
+    TRY(hsk_sort_passes(c, d_keys, c->alt.p, nullptr, nullptr, n, key_words, P,
+                        (uint64_t*)c->pass_hist.p, &in_b, st));
+    if (in_b) CK(cudaMemcpyAsync(d_keys, c->alt.p, n * kb, cudaMemcpyDeviceToDevice, st));
+    return read_device_error(c, st);
+}
+
+extern "C" int hsk_stage_rle(hsk_ctx* c, const uint64_t* d_sorted, uint64_t n, int key_words,
+                             uint32_t lo, uint32_t hi, void* stream, hsk_result* out) {
+    if (!c || !out || (n && !d_sorted) || (key_words != 1 && key_words != 2) || lo > hi) return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    c->zst = st;
+    const uint32_t H = c->cfg.hist_len;
+    TRY(hsk_ensure(c, c->hist, (size_t)H * 8, false));
+    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)H * 8, st));
+    CK(cudaMemsetAsync(c->small, 0, 64, st));
+    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+    c->ctr_used = 0;
+    Output O;
+    TRY(hsk_rle_chunk(c, d_sorted, n, key_words, lo, hi, H, (uint64_t*)c->hist.p, O, st));
+    TRY(read_device_error(c, st));
+    uint32_t mx = 0;
+    CK(cudaMemcpy(&mx, c->d_max, 4, cudaMemcpyDeviceToHost));
+    DevResult R;
+    memset(&R, 0, sizeof R);
+    R.n_pairs = O.n_pairs;
+    R.n_distinct = O.n_distinct;
+    R.n_windows = n;
+    R.max_count = mx;
+    R.key_words = key_words;
+    R.kmers = (const uint64_t*)c->out_keys.p;
+    R.counts = (const uint32_t*)c->out_counts.p;
+    R.hist = (const uint64_t*)c->hist.p;
+    R.hist_len = H;
+    R.n_chunks = 1;
+    to_public(R, out);
+    return HSK_OK;
+}
+
+extern "C" int hsk_stage_order(hsk_ctx* c, uint64_t* d_keys, uint32_t* d_counts, uint64_t n,
+                               int key_words, int key_bits, void* stream) {
+    if (!c || (n && (!d_keys || !d_counts)) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
+        key_bits > 64 * key_words)
+        return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    c->zst = st;
+    CK(cudaMemsetAsync(c->small, 0, 64, st));
+    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+    c->ctr_used = 0;
+    TRY(hsk_order_pairs(c, d_keys, d_counts, n, key_words, key_bits, st));
+    return read_device_error(c, st);
+}

@@ -1,0 +1,131 @@
+// hsk_runtime.h -- host-side state of a context (not part of the public ABI).
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hsk.h"
+
+#define HSK_N_COUNTERS 1024
+#define HSK_SMALL_BYTES 8192
+#define HSK_MAX_BUCKETS 8192
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct Encoded {
+    const uint64_t* packed = nullptr;
+    const uint64_t* invalid = nullptr;
+    const uint64_t* start = nullptr;
+    uint64_t n_bases = 0, n_pw = 0, n_mw = 0;
+};
+
+struct Supermers {
+    uint32_t B = 0;
+    std::vector<uint64_t> h_bucket_kmers;  // k-mers per bucket
+    std::vector<uint64_t> h_bucket_rec;    // first record of each bucket (+ total)
+    uint64_t n_records = 0, n_kmers = 0;
+    int rec_words = 2, nmax = 0;
+    const uint64_t* records = nullptr;
+};
+
+struct Output {
+    uint64_t n_pairs = 0;
+    uint64_t n_distinct = 0;
+};
+
+struct DevResult {
+    uint64_t n_pairs;
+    const uint64_t* kmers;
+    const uint32_t* counts;
+    const uint64_t* hist;
+    uint32_t hist_len;
+    int key_words;
+    uint64_t n_windows, n_distinct;
+    uint32_t max_count, n_chunks;
+    uint64_t n_supermers;
+    double device_ms;
+};
+
+struct HostResult {
+    DevResult R{};
+    std::vector<uint64_t> kmers;
+    std::vector<uint32_t> counts;
+    std::vector<uint64_t> hist;
+};
+
+struct ServeState;  // served form (hsk_serve.cu)
+
+struct hsk_ctx {
+    hsk_config cfg{};
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t zst = nullptr;  // stream of the call in progress (orders zero-fills)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err_msg;
+    size_t budget = 0, allocated = 0;
+    int fail_alloc_after = -1;
+
+    // small device scalars: error word, max count, run count, kept count, tile counters
+    void* small = nullptr;
+    int* d_err = nullptr;
+    uint32_t* d_max = nullptr;
+    uint64_t* d_nheads = nullptr;
+    uint64_t* d_nout = nullptr;
+    uint32_t* counters = nullptr;
+    uint32_t ctr_used = 0;
+    uint32_t epoch = 0;
+
+    // device arena
+    DevBuf in_reads, in_offsets;     // staged host inputs
+    DevBuf pk, iv, rs;               // S1 packed bases, invalid mask, read-start mask
+    DevBuf cta_cnt, cta_off, bucket_kmers, bucket_rec, records;  // S2/S3
+    DevBuf keys, alt, pass_hist, digit_off, lb_status;             // S4
+    DevBuf heads, out_keys, out_counts, hist;                      // S5
+    DevBuf pair_alt_keys, pair_alt_counts;                         // S6
+    DevBuf batch_a, batch_b, batch_c, batch_d;                     // batched form
+
+    void* h_pin = nullptr;
+    size_t h_pin_cap = 0;
+
+    HostResult host_res;                 // result of the last hsk_count
+    std::vector<HostResult> batch_res;   // results of the last hsk_count_batch
+
+    ServeState* serve = nullptr;
+
+    // profiling: events at stage boundaries (stage id of the span that ends there)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> marks;  // (event index, stage id; -1 = start)
+    double prof_ms[8] = {0};
+    uint64_t prof_passes = 0;
+
+    std::vector<DevBuf*> all_bufs() {
+        return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
+                &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &heads,
+                &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &batch_a,
+                &batch_b, &batch_c, &batch_d};
+    }
+};
+
+void hsk_set_error(hsk_ctx* c, const char* fmt, ...);
+int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new);
+int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
+                  uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
+                  DevResult& R);
+int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, uint64_t n_reads,
+                      int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st, DevBuf& d_reads,
+                      DevBuf& d_offsets, HostResult& HR);
+void hsk_serve_shutdown(hsk_ctx* c);

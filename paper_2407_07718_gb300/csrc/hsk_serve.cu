@@ -1,0 +1,325 @@
+// hsk_serve.cu -- batched and served forms of the counter.
+//
+// Served form (continuous batching): jobs are queued by hsk_submit and taken
+// by a fixed set of slots.  Each slot is a child context with its own stream
+// and its own device arena, kept resident between jobs, so admitted jobs run
+// concurrently on the device.  A queued job is admitted when a slot is free
+// and the device memory it needs -- estimated from its size -- fits the
+// budget next to what the other slots hold; idle slots give their arenas back
+// when a job would not fit otherwise.  Jobs complete in any order.
+//
+// Batched form: hsk_count_batch runs many independent read sets; see
+// hsk_batch.cu for the packed path.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "hsk_internal.h"
+#include "hsk_runtime.h"
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+enum TicketState { T_QUEUED = 0, T_RUNNING = 1, T_DONE = 2, T_CANCELED = 3 };
+
+struct Ticket {
+    hsk_job job{};
+    int state = T_QUEUED;
+    int rc = HSK_OK;
+    std::string err;
+    HostResult res;
+    size_t est = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct ServeState {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
+    uint64_t next_ticket = 1;
+    std::vector<hsk_ctx*> slots;
+    std::vector<size_t> slot_est;   // estimate of the running job (0 when idle)
+    std::vector<int> slot_busy;
+    std::vector<std::thread> workers;
+    size_t budget = 0;
+    bool stop = false;
+};
+
+// Device bytes a job needs at most (inputs, encoding, records, sort buffers,
+// output, fixed tables): an upper bound from its size alone.
+static size_t job_estimate(const hsk_job& j) {
+    uint64_t nb = j.n_reads ? j.offsets[j.n_reads] : 0;
+    double kb = j.k <= 32 ? 8.0 : 16.0;
+    double rec = j.k <= 32 ? 16.0 : 32.0;
+    double n = (double)nb;  // windows <= bases
+    double bytes = n * (1.0 + 0.25 + 0.25) + 8.0 * (double)(j.n_reads + 1) + n * rec / 2.0 +
+                   n * (2 * kb + 4 + 1 + kb + 4) + (96u << 20);
+    return (size_t)bytes;
+}
+
+static size_t slot_held(ServeState* S, int i) {
+    size_t h = S->slots[i]->allocated;
+    return S->slot_busy[i] ? std::max(h, S->slot_est[i]) : h;
+}
+
+static void trim_ctx(hsk_ctx* c) {
+    for (DevBuf* b : c->all_bufs()) {
+        if (b->p) {
+            cudaFree(b->p);
+            c->allocated -= b->cap;
+        }
+        b->p = nullptr;
+        b->cap = 0;
+    }
+}
+
+static void worker_main(hsk_ctx* parent, ServeState* S, int slot) {
+    hsk_ctx* c = S->slots[slot];
+    cudaSetDevice(parent->cfg.device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        Ticket* T = nullptr;
+        for (;;) {
+            if (S->stop) return;
+            if (!S->queue.empty()) {
+                uint64_t cand = S->queue.front();
+                Ticket* ct = S->tickets[cand].get();
+                size_t others = 0;
+                for (int i = 0; i < (int)S->slots.size(); ++i)
+                    if (i != slot) others += slot_held(S, i);
+                size_t mine = std::max(c->allocated, ct->est);
+                if (others + mine > S->budget) {
+                    // give back arenas of idle slots, then look again
+                    for (int i = 0; i < (int)S->slots.size(); ++i)
+                        if (i != slot && !S->slot_busy[i]) trim_ctx(S->slots[i]);
+                    others = 0;
+                    for (int i = 0; i < (int)S->slots.size(); ++i)
+                        if (i != slot) others += slot_held(S, i);
+                }
+                bool alone = true;
+                for (int i = 0; i < (int)S->slots.size(); ++i)
+                    if (i != slot && S->slot_busy[i]) alone = false;
+                // a job larger than the whole budget still runs when it is alone
+                // (its own allocations then fail with HSK_ENOMEM if it truly does not fit)
+                if (others + mine <= S->budget || alone) {
+                    T = ct;
+                    S->queue.pop_front();
+                    break;
+                }
+            }
+            S->cv_work.wait(lk);
+        }
+        T->state = T_RUNNING;
+        T->t_start = now_s();
+        S->slot_busy[slot] = 1;
+        S->slot_est[slot] = T->est;
+        hsk_job job = T->job;
+        lk.unlock();
+        HostResult hr;
+        int rc = hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo,
+                                   job.hi, c->stream, c->in_reads, c->in_offsets, hr);
+        std::string err = rc == HSK_OK ? std::string() : c->err_msg;
+        lk.lock();
+        T->rc = rc;
+        T->err = err;
+        T->res = std::move(hr);
+        T->res.R.kmers = T->res.kmers.data();
+        T->res.R.counts = T->res.counts.data();
+        T->res.R.hist = T->res.hist.data();
+        T->t_done = now_s();
+        T->state = T_DONE;
+        S->slot_busy[slot] = 0;
+        S->slot_est[slot] = 0;
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+}
+
+static int serve_start(hsk_ctx* c) {
+    if (c->serve) return HSK_OK;
+    ServeState* S = new ServeState();
+    S->budget = c->budget > c->allocated ? c->budget - c->allocated : 0;
+    int n_slots = 4;
+    for (int i = 0; i < n_slots; ++i) {
+        hsk_config cfg = c->cfg;
+        cfg.hbm_budget = S->budget;
+        hsk_ctx* child = nullptr;
+        int rc = hsk_create(&child, &cfg);
+        if (rc != HSK_OK) {
+            for (hsk_ctx* s : S->slots) hsk_destroy(s);
+            delete S;
+            hsk_set_error(c, "could not create serving slot %d", i);
+            return rc;
+        }
+        S->slots.push_back(child);
+        S->slot_est.push_back(0);
+        S->slot_busy.push_back(0);
+    }
+    c->serve = S;
+    for (int i = 0; i < n_slots; ++i) S->workers.emplace_back(worker_main, c, S, i);
+    return HSK_OK;
+}
+
+void hsk_serve_shutdown(hsk_ctx* c) {
+    if (!c || !c->serve) return;
+    ServeState* S = c->serve;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto& t : S->workers) t.join();
+    for (hsk_ctx* s : S->slots) hsk_destroy(s);
+    delete S;
+    c->serve = nullptr;
+}
+
+static int validate_job(hsk_ctx* c, const hsk_job* j) {
+    if (!j) return HSK_EINVAL;
+    if (j->k < 1 || j->k > 64 || j->m < 1 || j->m > j->k || j->m > 32 || j->lo > j->hi) {
+        hsk_set_error(c, "job has k=%d m=%d lo=%u hi=%u outside their ranges", j->k, j->m, j->lo, j->hi);
+        return HSK_EINVAL;
+    }
+    if (j->n_reads && !j->offsets) {
+        hsk_set_error(c, "job has NULL offsets");
+        return HSK_EINVAL;
+    }
+    if (j->n_reads && j->offsets[j->n_reads] > 0 && !j->reads) {
+        hsk_set_error(c, "job has NULL reads");
+        return HSK_EINVAL;
+    }
+    return HSK_OK;
+}
+
+extern "C" int hsk_submit(hsk_ctx* c, const hsk_job* job, uint64_t* ticket) {
+    if (!c || !ticket) return HSK_EINVAL;
+    int rc = validate_job(c, job);
+    if (rc != HSK_OK) return rc;
+    rc = serve_start(c);
+    if (rc != HSK_OK) return rc;
+    ServeState* S = c->serve;
+    auto T = std::make_unique<Ticket>();
+    T->job = *job;
+    T->est = job_estimate(*job);
+    T->t_submit = now_s();
+    std::lock_guard<std::mutex> g(S->mu);
+    uint64_t id = S->next_ticket++;
+    S->tickets[id] = std::move(T);
+    S->queue.push_back(id);
+    *ticket = id;
+    S->cv_work.notify_all();
+    return HSK_OK;
+}
+
+extern "C" int hsk_poll(hsk_ctx* c, uint64_t ticket, int* done) {
+    if (!c || !done) return HSK_EINVAL;
+    if (!c->serve) return HSK_ENOTFOUND;
+    ServeState* S = c->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return HSK_ENOTFOUND;
+    *done = it->second->state == T_DONE || it->second->state == T_CANCELED;
+    return HSK_OK;
+}
+
+static void fill_out(const HostResult& hr, hsk_result* out) {
+    memset(out, 0, sizeof(*out));
+    const DevResult& R = hr.R;
+    out->n_pairs = R.n_pairs;
+    out->kmers = hr.kmers.data();
+    out->counts = hr.counts.data();
+    out->hist = hr.hist.data();
+    out->hist_len = R.hist_len;
+    out->key_words = R.key_words;
+    out->n_windows = R.n_windows;
+    out->n_distinct = R.n_distinct;
+    out->max_count = R.max_count;
+    out->n_chunks = R.n_chunks;
+    out->n_supermers = R.n_supermers;
+    out->device_ms = R.device_ms;
+}
+
+extern "C" int hsk_wait(hsk_ctx* c, uint64_t ticket, hsk_result* out) {
+    if (!c || !out) return HSK_EINVAL;
+    if (!c->serve) return HSK_ENOTFOUND;
+    ServeState* S = c->serve;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return HSK_ENOTFOUND;
+    Ticket* T = it->second.get();
+    S->cv_done.wait(lk, [&] { return T->state == T_DONE || T->state == T_CANCELED; });
+    if (T->state == T_CANCELED) return HSK_ECANCELED;
+    if (T->rc != HSK_OK) {
+        c->err_msg = T->err;
+        return T->rc;
+    }
+    fill_out(T->res, out);
+    return HSK_OK;
+}
+
+extern "C" int hsk_cancel(hsk_ctx* c, uint64_t ticket) {
+    if (!c) return HSK_EINVAL;
+    if (!c->serve) return HSK_ENOTFOUND;
+    ServeState* S = c->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return HSK_ENOTFOUND;
+    if (it->second->state != T_QUEUED) return HSK_EINVAL;  // already running or finished
+    S->queue.erase(std::remove(S->queue.begin(), S->queue.end(), ticket), S->queue.end());
+    it->second->state = T_CANCELED;
+    S->cv_done.notify_all();
+    return HSK_OK;
+}
+
+extern "C" int hsk_release(hsk_ctx* c, uint64_t ticket) {
+    if (!c) return HSK_EINVAL;
+    if (!c->serve) return HSK_ENOTFOUND;
+    ServeState* S = c->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return HSK_ENOTFOUND;
+    if (it->second->state == T_QUEUED || it->second->state == T_RUNNING) return HSK_EINVAL;
+    S->tickets.erase(it);
+    return HSK_OK;
+}
+
+extern "C" int hsk_ticket_times(hsk_ctx* c, uint64_t ticket, double* queued_s, double* run_s) {
+    if (!c || !c->serve) return HSK_ENOTFOUND;
+    ServeState* S = c->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return HSK_ENOTFOUND;
+    Ticket* T = it->second.get();
+    if (T->state != T_DONE) return HSK_EINVAL;
+    if (queued_s) *queued_s = T->t_start - T->t_submit;
+    if (run_s) *run_s = T->t_done - T->t_start;
+    return HSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched form (first version: one context, jobs in order)
+// ---------------------------------------------------------------------------
+extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs, hsk_result* outs) {
+    if (!c || (n_jobs && (!jobs || !outs))) return HSK_EINVAL;
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        int rc = validate_job(c, jobs + i);
+        if (rc != HSK_OK) return rc;
+    }
+    cudaSetDevice(c->cfg.device);
+    c->batch_res.clear();
+    c->batch_res.resize(n_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        const hsk_job& j = jobs[i];
+        int rc = hsk_count_host_on(c, j.reads, j.offsets, j.n_reads, j.k, j.m, j.lo, j.hi, c->stream,
+                                   c->in_reads, c->in_offsets, c->batch_res[i]);
+        if (rc != HSK_OK) return rc;
+    }
+    for (uint32_t i = 0; i < n_jobs; ++i) fill_out(c->batch_res[i], outs + i);
+    return HSK_OK;
+}

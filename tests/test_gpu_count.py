@@ -1,0 +1,145 @@
+"""End-to-end parity of hsk_count / hsk_count_device with the CPU oracle:
+bit-exact (k-mer, count) pairs, histogram, window / distinct / max counts."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from gpu_util import assert_same_result, dev, dev_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return datagen.tiny()
+
+
+def test_tiny_workload_bit_exact(hsk, tiny):
+    """1 Mbp genome, 20,000 x 150 bp reads, k=31, m=17, filter [2, 1000]."""
+    want = oracle.count(tiny.reads, tiny.offsets, tiny.k, tiny.lo, tiny.hi)
+    with hsk.Context() as ctx:
+        got = ctx.count(tiny.reads, tiny.offsets, tiny.k, tiny.m, tiny.lo, tiny.hi)
+        assert_same_result(got, want, "tiny")
+        assert got.n_windows == 20_000 * 120
+        # device-pointer entry point gives the same bytes
+        r = ctx.count_device(dev(tiny.reads), dev_u64(tiny.offsets), tiny.k, tiny.m, tiny.lo, tiny.hi)
+        assert_same_result(ctx.result_to_host(r), want, "tiny-device")
+
+
+@pytest.mark.parametrize("k,m", [(1, 1), (2, 1), (11, 6), (16, 8), (21, 11), (31, 17), (32, 16), (33, 17),
+                                 (47, 23), (55, 21), (63, 31), (64, 32), (64, 1)])
+def test_k_range_with_invalid_bases(hsk, k, m):
+    reads, offs = datagen.random_reads(k * 31 + m, 400, 0, 600, p_invalid=0.005, invalid=b"NnRY.")
+    # low-complexity reads so many k-mers repeat at every k
+    extra = ["ACGT" * 50, "AAAAAAAAAA" * 20, "GATTACA" * 30, "T" * 65, "CG" * 40]
+    strs = [reads[offs[i]:offs[i + 1]].tobytes().decode() for i in range(len(offs) - 1)] + extra
+    o = np.zeros(len(strs) + 1, np.uint64)
+    o[1:] = np.cumsum([len(s) for s in strs])
+    r = np.frombuffer("".join(strs).encode(), np.uint8).copy()
+    want = oracle.count(r, o, k, 1, 1 << 31, hist_len=256)
+    with hsk.Context(hist_len=256) as ctx:
+        got = ctx.count(r, o, k, m, 1, 1 << 31)
+    assert_same_result(got, want, f"k={k} m={m}")
+
+
+@pytest.mark.parametrize("n_buckets", [1, 3, 256, 8192])
+def test_result_independent_of_bucket_count(hsk, tiny, n_buckets):
+    n = 5000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    want = oracle.count(reads, offs, 31, 2, 1000)
+    with hsk.Context(n_buckets=n_buckets) as ctx:
+        assert_same_result(ctx.count(reads, offs, 31, 17, 2, 1000), want, f"B={n_buckets}")
+
+
+@pytest.mark.parametrize("m", [1, 9, 16, 31])
+def test_result_independent_of_m(hsk, tiny, m):
+    n = 3000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    want = oracle.count(reads, offs, 31, 1, 10)
+    with hsk.Context() as ctx:
+        assert_same_result(ctx.count(reads, offs, 31, m, 1, 10), want, f"m={m}")
+
+
+@pytest.mark.parametrize("k", [31, 55])
+def test_chunked_sort_and_output_order(hsk, tiny, k):
+    """Force many sort chunks (S6 then orders the pairs of all chunks)."""
+    n = 6000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    want = oracle.count(reads, offs, k, 1, 5)
+    with hsk.Context(n_buckets=512, max_chunk_kmers=40_000) as ctx:
+        got = ctx.count(reads, offs, k, 17, 1, 5)
+    assert got.n_chunks > 5
+    assert_same_result(got, want, "chunked")
+
+
+def test_edge_cases(hsk):
+    with hsk.Context(hist_len=16) as ctx:
+        # empty input
+        r = ctx.count(np.zeros(0, np.uint8), np.zeros(1, np.uint64), 31, 17, 2, 10)
+        assert r.n_windows == 0 and r.kmers.size == 0 and not r.hist.any()
+        # only empty reads
+        r = ctx.count(np.zeros(0, np.uint8), np.zeros(5, np.uint64), 31, 17, 2, 10)
+        assert r.n_windows == 0
+        # reads shorter than k, all invalid, and one exact-length read
+        strs = ["ACGT", "NNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNN", "A" * 31, "acgtacgtacgtacgtacgtacgtacgtacgt"]
+        o = np.zeros(len(strs) + 1, np.uint64)
+        o[1:] = np.cumsum([len(s) for s in strs])
+        b = np.frombuffer("".join(strs).encode(), np.uint8).copy()
+        r = ctx.count(b, o, 31, 17, 1, 10)
+        assert r.n_windows == 1 and r.kmers.tolist() == [0] and r.counts.tolist() == [1]
+        # histogram last bin collects counts >= hist_len - 1
+        s = "A" * 200
+        r = ctx.count(np.frombuffer(s.encode(), np.uint8).copy(), np.array([0, 200], np.uint64), 5, 3, 1, 1000)
+        assert r.max_count == 196 and int(r.hist[15]) == 1 and int(r.hist.sum()) == 1
+
+
+def test_argument_errors(hsk, tiny):
+    n = 10
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    with hsk.Context() as ctx:
+        for k, m, lo, hi in [(0, 1, 1, 2), (65, 17, 1, 2), (31, 0, 1, 2), (31, 32, 1, 2), (20, 21, 1, 2),
+                             (31, 17, 5, 4)]:
+            with pytest.raises(hsk.HskError) as e:
+                ctx.count(reads, offs, k, m, lo, hi)
+            assert e.value.code == hsk.HSK_EINVAL
+        bad = offs.copy()
+        bad[3], bad[4] = bad[4], bad[3]
+        with pytest.raises(hsk.HskError) as e:
+            ctx.count(reads, bad, 31, 17, 2, 8)
+        assert e.value.code == hsk.HSK_EINVAL
+        # device-side offset check: last offset must equal n_bases
+        with pytest.raises(hsk.HskError) as e:
+            ctx.count_device(dev(reads), dev_u64(offs), 31, 17, 2, 8, n_bases=int(offs[-1]) + 5)
+        assert e.value.code == hsk.HSK_EINVAL
+        # the context still works afterwards
+        assert_same_result(ctx.count(reads, offs, 31, 17, 1, 9), oracle.count(reads, offs, 31, 1, 9))
+
+
+def test_budget_and_injected_allocation_failure(hsk, tiny):
+    n = 2000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    want = oracle.count(reads, offs, 31, 2, 100)
+    with hsk.Context(hbm_budget=8 << 20) as ctx:
+        with pytest.raises(hsk.HskError) as e:
+            ctx.count(reads, offs, 31, 17, 2, 100)
+        assert e.value.code == hsk.HSK_ENOMEM
+    with hsk.Context() as ctx:
+        for i in range(6):
+            ctx.fail_alloc_after(i)
+            with pytest.raises(hsk.HskError) as e:
+                ctx.count(reads, offs, 31, 17, 2, 100)
+            assert e.value.code == hsk.HSK_ENOMEM
+            ctx.fail_alloc_after(-1)
+            assert_same_result(ctx.count(reads, offs, 31, 17, 2, 100), want, f"after failure {i}")
+
+
+def test_repeated_calls_reuse_the_arena(hsk, tiny):
+    """The same context gives identical bytes call after call (look-back epochs,
+    tile counters and buffers are reused)."""
+    n = 4000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    want = oracle.count(reads, offs, 31, 2, 50)
+    with hsk.Context() as ctx:
+        for i in range(25):
+            assert_same_result(ctx.count(reads, offs, 31, 17, 2, 50), want, f"call {i}")
