@@ -55,7 +55,7 @@ typedef struct {
     int device;            /* CUDA device ordinal */
     uint64_t hbm_budget;   /* bytes of device memory the context may hold; 0 = 90 % of free */
     uint32_t hist_len;     /* histogram bins, >= 2 (default 65536) */
-    uint32_t n_buckets;    /* minimizer buckets (tasks); 0 = chosen per job */
+    uint32_t n_buckets;    /* minimizer buckets (tasks), a power of two <= 8192; 0 = per job */
     uint32_t radix_bits;   /* LSD digit width, 8 (default) */
     uint32_t max_chunk_kmers; /* 0 = as many as the budget allows; else cap per sort chunk */
     uint64_t seed;         /* XOR-ed into each canonical m-mer before hashing */

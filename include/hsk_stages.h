@@ -54,7 +54,7 @@ int hsk_stage_windows(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offse
 
 /* Stage S3, supermers scattered into minimizer-hashed buckets (Sec. 2.4,
  * Sec. 3.2; the buckets are the tasks of Sec. 3.4).  A window's bucket is
- * floor(minhash * n_buckets / 2^64); a supermer is a run of consecutive valid
+ * minhash mod n_buckets (n_buckets a power of two, 1..8192); a supermer is a run of consecutive valid
  * windows of one read with equal buckets, cut at most every max_kmers windows
  * (and where the implementation's tiles end).  Outputs: d_bucket_kmers
  * (caller, n_buckets words) = k-mers per bucket; d_bucket_rec (caller,

@@ -29,7 +29,7 @@
 //   k-mer before the filter, with bin H-1 collecting counts >= H-1; the filter
 //   is inclusive [lo, hi]; output is in ascending key order; the m-mer score is
 //   MurmurHash3's 64-bit finalizer applied to (canonical m-mer XOR seed); the
-//   bucket of a window is floor(minhash * B / 2^64).
+//   bucket of a window is minhash mod B, the remainder rule of Sec. 3.2.
 
 #include <algorithm>
 #include <cstdint>
@@ -102,8 +102,10 @@ static uint64_t mmer_score(const char* s, int m, uint64_t seed) {
     return fmix64((uint64_t)canonical_code(s, m) ^ seed);
 }
 
+// Target of a minimizer (Sec. 3.2): the remainder of its hash value divided
+// by the number of targets.
 static uint32_t bucket_of(uint64_t minhash, uint32_t n_buckets) {
-    return (uint32_t)(((u128)minhash * (u128)n_buckets) >> 64);
+    return (uint32_t)(minhash % n_buckets);
 }
 
 extern "C" {
@@ -329,9 +331,8 @@ uint64_t oracle_windows(const char* reads, const uint64_t* offsets, uint64_t n_r
 }
 
 // Stage reference, supermers and buckets (Sec. 2.4; Sec. 3.2; tasks of
-// Sec. 3.4).  A window's bucket is floor(minhash * n_buckets / 2^64), the
-// multiply-shift form of "hash value modulo the number of targets".  A
-// supermer is a maximal run of windows of one read that start at consecutive
+// Sec. 3.4).  A window's bucket is minhash mod n_buckets, the remainder of the
+// minimizer's hash divided by the number of targets (Sec. 3.2).  A supermer is a maximal run of windows of one read that start at consecutive
 // positions and have equal buckets; its overlapping bases are stored once.
 // Writes, per supermer in read order: global start position, number of
 // k-mers, bucket; and per bucket its number of k-mers.  Returns the number of

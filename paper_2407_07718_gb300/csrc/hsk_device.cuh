@@ -126,9 +126,11 @@ __device__ __forceinline__ u64 fmix64(u64 h) {
     return h;
 }
 
-// Bucket (task) of a minimizer score: floor(score * n_buckets / 2^64).
+// Bucket (task) of a minimizer score: the remainder of the score divided by
+// the number of buckets (Sec. 3.2); n_buckets is a power of two, so the
+// remainder is a mask of the low bits.
 __device__ __forceinline__ uint32_t bucket_of(u64 score, uint32_t n_buckets) {
-    return (uint32_t)__umul64hi(score, (u64)n_buckets);
+    return (uint32_t)score & (n_buckets - 1u);
 }
 
 // ---------------------------------------------------------------------------

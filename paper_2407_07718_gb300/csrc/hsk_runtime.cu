@@ -161,6 +161,8 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
     if (cfg_in) cfg = *cfg_in;
     else hsk_config_default(&cfg);
     if (cfg.hist_len < 2 || (cfg.radix_bits != 0 && cfg.radix_bits != 8)) return HSK_EINVAL;
+    if (cfg.n_buckets && (cfg.n_buckets > HSK_MAX_BUCKETS || (cfg.n_buckets & (cfg.n_buckets - 1))))
+        return HSK_EINVAL;  // a power of two: the bucket is a mask of the hash
     hsk_ctx* c = new hsk_ctx();
     c->cfg = cfg;
     cudaError_t e = cudaSetDevice(cfg.device);
@@ -799,7 +801,7 @@ extern "C" int hsk_stage_supermers(hsk_ctx* c, const char* d_reads, const uint64
                                    uint64_t* n_records, int* record_words, int* max_kmers,
                                    void* stream) {
     TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
-    if (n_buckets < 1 || n_buckets > HSK_MAX_BUCKETS || !d_bucket_kmers || !d_bucket_rec || !d_records ||
+    if (n_buckets < 1 || n_buckets > HSK_MAX_BUCKETS || (n_buckets & (n_buckets - 1)) || !d_bucket_kmers || !d_bucket_rec || !d_records ||
         !n_records || !record_words)
         return HSK_EINVAL;
     CK(cudaSetDevice(c->cfg.device));

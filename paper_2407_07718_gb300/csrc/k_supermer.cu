@@ -3,8 +3,8 @@
 //
 // Sec. 3.2: every m-mer is scored by a hash (here MurmurHash3's fmix64 of the
 // canonical m-mer XOR a seed); a k-mer's minimizer is its lowest-scoring
-// m-mer, and the same hash value decides the k-mer's target, here a bucket
-// floor(score * B / 2^64).  Sec. 2.4: consecutive k-mers with the same target
+// m-mer, and the same hash value decides the k-mer's target: bucket
+// score mod B (B a power of two).  Sec. 2.4: consecutive k-mers with the same target
 // form a supermer whose overlapping bases are stored once.  Sec. 3.4: the
 // buckets are the paper's tasks -- a k-mer value never lands in two of them,
 // because canonical m-mers give a k-mer and its reverse complement the same

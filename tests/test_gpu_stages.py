@@ -88,8 +88,8 @@ def _record_kmers(words, rw, k):
     return n, out
 
 
-@pytest.mark.parametrize("k,m,B", [(31, 17, 64), (31, 17, 1), (21, 11, 3), (55, 21, 128), (16, 8, 4096),
-                                   (64, 31, 7)])
+@pytest.mark.parametrize("k,m,B", [(31, 17, 64), (31, 17, 1), (21, 11, 4), (55, 21, 128), (16, 8, 4096),
+                                   (64, 31, 8), (33, 5, 8192)])
 def test_s3_supermers(hsk, k, m, B):
     import torch
     reads, offs = _inputs(k + B, n_reads=150, lo=0, hi=2500)
@@ -97,7 +97,7 @@ def test_s3_supermers(hsk, k, m, B):
     _, _, _, want_bk = oracle.supermers(reads, offs, k, m, B)
     want = Counter()
     for i in range(len(pos)):
-        want[((int(mh[i]) * B) >> 64, int(key[i, 0]) | (int(key[i, 1]) << 64))] += 1
+        want[(int(mh[i]) % B, int(key[i, 0]) | (int(key[i, 1]) << 64))] += 1
     with hsk.Context() as ctx:
         bk = empty_dev(B, torch.int64)
         br = empty_dev(B + 1, torch.int64)

@@ -264,7 +264,7 @@ def test_supermers_against_brute_force_runs(n_buckets):
     reads, offs = datagen.random_reads(17, 80, 0, 200, p_invalid=0.01)
     k, m = 21, 11
     pos, key, mh, _ = oracle.windows(reads, offs, k, m)
-    bucket = [(int(h) * n_buckets) >> 64 for h in mh]
+    bucket = [int(h) % n_buckets for h in mh]
     read_of = np.searchsorted(offs, pos, side="right") - 1
     want = []
     i = 0
