@@ -126,8 +126,8 @@ def test_budget_and_injected_allocation_failure(hsk, tiny):
         with pytest.raises(hsk.HskError) as e:
             ctx.count(reads, offs, 31, 17, 2, 100)
         assert e.value.code == hsk.HSK_ENOMEM
-    with hsk.Context() as ctx:
-        for i in range(6):
+    for i in range(8):  # the i-th device allocation of a fresh context fails
+        with hsk.Context() as ctx:
             ctx.fail_alloc_after(i)
             with pytest.raises(hsk.HskError) as e:
                 ctx.count(reads, offs, 31, 17, 2, 100)
