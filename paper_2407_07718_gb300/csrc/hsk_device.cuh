@@ -153,6 +153,9 @@ __device__ __forceinline__ void st_relaxed(u64* p, u64 v) {
 constexpr u64 LB_AGG = 1ULL << 62;
 constexpr u64 LB_PREFIX = 2ULL << 62;
 constexpr u64 LB_VALUE = (1ULL << 48) - 1;
+// Words between the status words of consecutive tiles in one-value look-backs:
+// one 32-byte L2 sector per tile, so neighbouring tiles never write the same sector.
+constexpr int LB_PAD = 4;
 __device__ __forceinline__ u64 lb_word(u64 flag, uint32_t epoch, u64 value) {
     return flag | ((u64)(epoch & 0x3FFF) << 48) | (value & LB_VALUE);
 }
@@ -181,6 +184,50 @@ __device__ __forceinline__ u64 lookback_exclusive(u64* status, u64 stride, u64 t
         excl += s & LB_VALUE;
         if (fl == LB_PREFIX) break;
         --j;
+    }
+    return excl;
+}
+
+// The same look-back with WIN status words loaded per round trip: the WIN
+// predecessors' words are read independently, then consumed in order until a
+// word is not ready (re-read from there) or carries an inclusive prefix.  On
+// this GPU a status word can sit in the far die's L2, so one dependent read
+// costs ~1 us; reading WIN at a time divides the chain of waits by WIN.
+template <int WIN>
+__device__ __forceinline__ u64 lookback_exclusive_win(u64* status, u64 stride, u64 tile,
+                                                      uint32_t epoch, int* err) {
+    u64 excl = 0;
+    long long j = (long long)tile - 1;
+    uint32_t spins = 0;
+    const uint32_t ep_want = epoch & 0x3FFF;
+    while (j >= 0) {
+        u64 s[WIN];
+#pragma unroll
+        for (int i = 0; i < WIN; ++i) s[i] = (j - i >= 0) ? ld_relaxed(status + (u64)(j - i) * stride) : 0ULL;
+        int used = 0;
+        bool done = false;
+#pragma unroll
+        for (int i = 0; i < WIN; ++i) {
+            if (done || used != i) continue;  // stop at the first word not consumed
+            if (j - i < 0) {
+                done = true;
+                continue;
+            }
+            u64 fl = s[i] & (3ULL << 62);
+            if (fl == 0 || ((uint32_t)(s[i] >> 48) & 0x3FFF) != ep_want) continue;  // not ready
+            excl += s[i] & LB_VALUE;
+            used = i + 1;
+            if (fl == LB_PREFIX) done = true;
+        }
+        if (done) break;
+        if (used == 0) {
+            if (++spins > HSK_SPIN_LIMIT) {
+                raise_error(err, HSK_DERR_TIMEOUT);
+                break;
+            }
+            if (spins > 64) __nanosleep(64);
+        }
+        j -= used;
     }
     return excl;
 }

@@ -66,28 +66,34 @@ void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* st
                      uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st);
 
 // ---- S4 sort ---------------------------------------------------------------
-// Expand records [0, n_rec) into canonical keys (in record order) and add the
-// per-pass digit histograms of the keys into hist[n_pass][256].
-void launch_expand(const uint64_t* records, uint64_t n_rec, int rec_words, int k, void* keys,
-                   uint64_t n_keys, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch,
-                   uint64_t* hist, int n_pass, int* err, int grid, cudaStream_t st);
+// Segment c: records [rec_base[c], rec_base[c+1]) expand to keys
+// [key_base[c], key_base[c+1]); hist[c][p][256] receives the segment's digit
+// histograms.  tile_ctrs: C zeroed counters; status: C * (max_tiles + 1) words.
+uint64_t expand_tiles(uint64_t n_rec);
 int expand_grid(int num_sms);
-uint64_t expand_status_words(uint64_t n_rec);
+void launch_expand_seg(const uint64_t* records, const uint64_t* rec_base, const uint64_t* key_base,
+                       uint32_t C, uint64_t max_tiles, int k, void* keys, uint64_t* status,
+                       uint32_t* tile_ctrs, uint32_t epoch, uint64_t* hist, int n_pass, int* err,
+                       int grid, cudaStream_t st);
 
-// Digit histograms of plain keys (stage sort and pair order).
+// Digit histograms of plain keys (one segment): hist[p][256].
 void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hist, int n_pass,
                        int grid, cudaStream_t st);
-// digit_off[p][d] = exclusive prefix over d of hist[p][d]
-void launch_digit_offsets(const uint64_t* hist, uint64_t* digit_off, int n_pass, cudaStream_t st);
+// doff[p][c][d] = key_base[c] + exclusive prefix over d of hist[c][p][d]
+void launch_digit_offsets_seg(const uint64_t* hist, const uint64_t* key_base, uint64_t* doff, int n_pass,
+                              uint32_t C, cudaStream_t st);
 
-// One LSD pass over n keys (optionally carrying uint32 values).
-uint64_t onesweep_tiles(uint64_t n, int key_words);
-void launch_onesweep(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, uint64_t n,
-                     int key_words, int shift, const uint64_t* digit_off, uint64_t* status,
-                     uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st);
+// One LSD pass over C segments (tmax = most tiles of any segment), optionally
+// carrying uint32 values; status: C * tmax * 256 words; doff: this pass's [C][256].
+uint64_t onesweep_tile_keys(int key_words);
+void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
+                         const uint64_t* key_base, uint32_t C, uint32_t tmax, int key_words, int shift,
+                         const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err,
+                         cudaStream_t st);
 
 // ---- S5 run-length count, filter, histogram -------------------------------
 uint64_t rle_tiles(uint64_t n, int key_words);
+uint64_t rle_status_words(uint64_t n);  // look-back words for n items
 // heads[0..D) = start index of every run; heads[D] = n; *n_heads = D.
 void launch_rle_heads(const void* keys, uint64_t n, int key_words, uint32_t* heads,
                       uint64_t* n_heads, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch,

@@ -425,28 +425,83 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
 
 static int n_passes_for(int key_bits) { return (key_bits + 7) / 8; }
 
-// LSD sort of n keys in a (b is scratch of the same size); *sorted_in_b tells
-// where the result ended.  hist[n_pass][256] must hold the digit histograms.
-int hsk_sort_passes(hsk_ctx* c, void* a, void* b, uint32_t* va, uint32_t* vb, uint64_t n,
-                    int key_words, int n_pass, uint64_t* hist, bool* sorted_in_b, cudaStream_t st,
-                    bool make_offsets = true) {
+// C zeroed tile counters in a row for one launch.
+static int next_counters(hsk_ctx* c, cudaStream_t st, uint32_t n, uint32_t** ctr) {
+    if (n > HSK_N_COUNTERS) {
+        hsk_set_error(c, "%u tile counters requested", n);
+        return HSK_EINVAL;
+    }
+    if (c->ctr_used + n > HSK_N_COUNTERS) {
+        CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+        c->ctr_used = 0;
+    }
+    *ctr = c->counters + c->ctr_used;
+    c->ctr_used += n;
+    return HSK_OK;
+}
+
+// Segment boundaries (C + 1 key offsets, and record offsets when given) to
+// the device; the host arrays are copied before the call returns.
+static int upload_segments(hsk_ctx* c, const std::vector<uint64_t>& key_base,
+                           const std::vector<uint64_t>* rec_base, cudaStream_t st) {
+    size_t n = key_base.size();
+    TRY(hsk_ensure(c, c->seg, 2 * n * 8, false));
+    CK(cudaMemcpyAsync(c->seg.p, key_base.data(), n * 8, cudaMemcpyHostToDevice, st));
+    if (rec_base)
+        CK(cudaMemcpyAsync((uint64_t*)c->seg.p + n, rec_base->data(), n * 8, cudaMemcpyHostToDevice, st));
+    return HSK_OK;
+}
+
+// LSD passes over C segments of keys in a (b is scratch of the same size);
+// the digit offsets doff[P][C][256] must be ready.  *sorted_in_b tells where
+// the result ended.
+static int sort_segments(hsk_ctx* c, void* a, void* b, uint32_t* va, uint32_t* vb, const uint64_t* d_key_base,
+                         uint32_t C, uint32_t tmax, int key_words, int n_pass, const uint64_t* doff,
+                         bool* sorted_in_b, cudaStream_t st) {
     *sorted_in_b = false;
-    if (n == 0 || n_pass == 0) return HSK_OK;
-    TRY(ensure_status(c, onesweep_tiles(n, key_words) * 256 + 1, st));
-    if (make_offsets) launch_digit_offsets(hist, (uint64_t*)c->digit_off.p, n_pass, st);
+    if (tmax == 0 || n_pass == 0) return HSK_OK;
+    TRY(ensure_status(c, (uint64_t)C * tmax * 256 + 1, st));
     void *src = a, *dst = b;
     uint32_t *vs = va, *vd = vb;
     for (int p = 0; p < n_pass; ++p) {
         uint32_t ep, *ctr;
         TRY(hsk_next_epoch(c, st, &ep));
         TRY(hsk_next_counter(c, st, &ctr));
-        launch_onesweep(src, dst, vs, vd, n, key_words, 8 * p, (uint64_t*)c->digit_off.p + 256 * p,
-                        (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+        launch_onesweep_seg(src, dst, vs, vd, d_key_base, C, tmax, key_words, 8 * p, doff + (size_t)p * C * 256,
+                            (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
         std::swap(src, dst);
         std::swap(vs, vd);
     }
     CK(cudaGetLastError());
     *sorted_in_b = (n_pass % 2) == 1;
+    return HSK_OK;
+}
+
+// A plain (one-segment) sort of n keys (with optional values) in place.
+static int plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int key_words, int key_bits,
+                      DevBuf& alt_keys, DevBuf* alt_vals, cudaStream_t st) {
+    if (n <= 1) return HSK_OK;
+    size_t kb = (size_t)key_words * 8;
+    int P = (key_bits + 7) / 8;
+    TRY(hsk_ensure(c, alt_keys, n * kb, false));
+    if (vals) TRY(hsk_ensure(c, *alt_vals, n * 4, false));
+    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
+    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
+    std::vector<uint64_t> kb0 = {0, n};
+    TRY(upload_segments(c, kb0, nullptr, st));
+    CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
+    launch_digit_hist(keys, key_words, n, (uint64_t*)c->pass_hist.p, P, c->num_sms * 4, st);
+    launch_digit_offsets_seg((uint64_t*)c->pass_hist.p, (const uint64_t*)c->seg.p, (uint64_t*)c->digit_off.p, P,
+                             1, st);
+    uint32_t tmax = (uint32_t)((n + onesweep_tile_keys(key_words) - 1) / onesweep_tile_keys(key_words));
+    bool in_b = false;
+    TRY(sort_segments(c, keys, alt_keys.p, vals, vals ? (uint32_t*)alt_vals->p : nullptr,
+                      (const uint64_t*)c->seg.p, 1, tmax, key_words, P, (const uint64_t*)c->digit_off.p, &in_b,
+                      st));
+    if (in_b) {
+        CK(cudaMemcpyAsync(keys, alt_keys.p, n * kb, cudaMemcpyDeviceToDevice, st));
+        if (vals) CK(cudaMemcpyAsync(vals, alt_vals->p, n * 4, cudaMemcpyDeviceToDevice, st));
+    }
     return HSK_OK;
 }
 
@@ -459,7 +514,7 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
         return HSK_EOVERFLOW;
     }
     TRY(hsk_ensure(c, c->heads, (n + 1) * 4, false));
-    TRY(ensure_status(c, rle_tiles(n, key_words) + 1, st));
+    TRY(ensure_status(c, rle_status_words(n), st));
     uint32_t ep, *ctr;
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
@@ -487,7 +542,7 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
         c->out_keys = nk;
         c->out_counts = ncn;
     }
-    TRY(ensure_status(c, rle_tiles(D, key_words) + 1, st));
+    TRY(ensure_status(c, rle_status_words(D), st));
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
     launch_rle_emit(sorted, (const uint32_t*)c->heads.p, c->d_nheads, D, key_words, lo, hi, d_hist,
@@ -502,26 +557,30 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
     return HSK_OK;
 }
 
-// Order the output pairs by key (stage S6), needed only for multi-chunk jobs.
+// Order the output pairs by key (stage S6): segments and chunks are groups
+// of minimizer buckets, so their pairs come out in bucket order.
 int hsk_order_pairs(hsk_ctx* c, void* keys, uint32_t* counts, uint64_t n, int key_words,
                     int key_bits, cudaStream_t st) {
-    if (n <= 1) return HSK_OK;
-    size_t kb = (size_t)key_words * 8;
-    int P = n_passes_for(key_bits);
-    TRY(hsk_ensure(c, c->pair_alt_keys, n * kb, false));
-    TRY(hsk_ensure(c, c->pair_alt_counts, n * 4, false));
-    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
-    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
-    CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
-    launch_digit_hist(keys, key_words, n, (uint64_t*)c->pass_hist.p, P, c->num_sms * 4, st);
-    bool in_b = false;
-    TRY(hsk_sort_passes(c, keys, c->pair_alt_keys.p, counts, (uint32_t*)c->pair_alt_counts.p, n,
-                        key_words, P, (uint64_t*)c->pass_hist.p, &in_b, st));
-    if (in_b) {
-        CK(cudaMemcpyAsync(keys, c->pair_alt_keys.p, n * kb, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(counts, c->pair_alt_counts.p, n * 4, cudaMemcpyDeviceToDevice, st));
+    return plain_sort(c, keys, counts, n, key_words, key_bits, c->pair_alt_keys, &c->pair_alt_counts, st);
+}
+
+// Split buckets [b0, b1) into at most C_want groups of roughly equal k-mer
+// counts; returns the first bucket of every group and b1.
+static std::vector<uint32_t> group_buckets(const Supermers& S, uint32_t b0, uint32_t b1, uint32_t C_want) {
+    uint64_t total = 0;
+    for (uint32_t b = b0; b < b1; ++b) total += S.h_bucket_kmers[b];
+    std::vector<uint32_t> cut = {b0};
+    uint64_t acc = 0;
+    uint32_t made = 1;
+    for (uint32_t b = b0; b < b1; ++b) {
+        acc += S.h_bucket_kmers[b];
+        if (b + 1 < b1 && made < C_want && acc * C_want >= total * made) {
+            cut.push_back(b + 1);
+            ++made;
+        }
     }
-    return HSK_OK;
+    cut.push_back(b1);
+    return cut;
 }
 
 // Plan chunks of consecutive buckets whose keys fit the sort budget.
@@ -587,36 +646,58 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     std::vector<std::pair<uint32_t, uint32_t>> chunks;
     if (S.n_kmers > 0) TRY(hsk_plan_chunks(c, S, kw, chunks));
     const int P = n_passes_for(2 * k);
-    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
-    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
+    uint32_t total_segments = 0;
     for (auto& ch : chunks) {
-        uint64_t r0 = S.h_bucket_rec[ch.first], r1 = S.h_bucket_rec[ch.second];
         uint64_t nk = 0;
         for (uint32_t b = ch.first; b < ch.second; ++b) nk += S.h_bucket_kmers[b];
         if (nk == 0) continue;
+        // segments: groups of buckets sorted independently, tiles interleaved
+        uint32_t C_want = (uint32_t)std::min<uint64_t>({(uint64_t)HSK_SEGMENTS, ch.second - ch.first,
+                                                        std::max<uint64_t>(1, nk / HSK_MIN_SEGMENT_KMERS)});
+        std::vector<uint32_t> cut = group_buckets(S, ch.first, ch.second, C_want);
+        const uint32_t C = (uint32_t)cut.size() - 1;
+        total_segments += C;
+        std::vector<uint64_t> kbase(C + 1), rbase(C + 1);
+        uint64_t acc = 0, max_rt = 0, max_kt = 0;
+        const uint64_t tk = onesweep_tile_keys(kw);
+        for (uint32_t sgi = 0; sgi < C; ++sgi) {
+            kbase[sgi] = acc;
+            rbase[sgi] = S.h_bucket_rec[cut[sgi]];
+            uint64_t sk = 0;
+            for (uint32_t b = cut[sgi]; b < cut[sgi + 1]; ++b) sk += S.h_bucket_kmers[b];
+            acc += sk;
+            max_rt = std::max<uint64_t>(max_rt, expand_tiles(S.h_bucket_rec[cut[sgi + 1]] - rbase[sgi]));
+            max_kt = std::max<uint64_t>(max_kt, (sk + tk - 1) / tk);
+        }
+        kbase[C] = acc;
+        rbase[C] = S.h_bucket_rec[cut[C]];
         TRY(hsk_ensure(c, c->keys, nk * kb, false));
         TRY(hsk_ensure(c, c->alt, nk * kb, false));
-        TRY(ensure_status(c, expand_status_words(r1 - r0), st));
-        CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
-        uint32_t ep, *ctr;
+        TRY(hsk_ensure(c, c->pass_hist, (size_t)C * P * 256 * 8, false));
+        TRY(hsk_ensure(c, c->digit_off, (size_t)C * P * 256 * 8, false));
+        TRY(ensure_status(c, (uint64_t)C * (max_rt + 1) * 4 + 4, st));
+        TRY(upload_segments(c, kbase, &rbase, st));
+        const uint64_t* d_kbase = (const uint64_t*)c->seg.p;
+        const uint64_t* d_rbase = d_kbase + (C + 1);
+        CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)C * P * 256 * 8, st));
+        uint32_t ep, *ctrs;
         TRY(hsk_next_epoch(c, st, &ep));
-        TRY(hsk_next_counter(c, st, &ctr));
-        launch_expand(S.records + r0 * S.rec_words, r1 - r0, S.rec_words, k, c->keys.p, nk,
-                      (uint64_t*)c->lb_status.p, ctr, ep, (uint64_t*)c->pass_hist.p, P, c->d_err,
-                      expand_grid(c->num_sms), st);
+        TRY(next_counters(c, st, C, &ctrs));
+        launch_expand_seg(S.records, d_rbase, d_kbase, C, max_rt, k, c->keys.p, (uint64_t*)c->lb_status.p, ctrs,
+                          ep, (uint64_t*)c->pass_hist.p, P, c->d_err, expand_grid(c->num_sms), st);
+        launch_digit_offsets_seg((uint64_t*)c->pass_hist.p, d_kbase, (uint64_t*)c->digit_off.p, P, C, st);
         CK(cudaGetLastError());
-        launch_digit_offsets((uint64_t*)c->pass_hist.p, (uint64_t*)c->digit_off.p, P, st);
         prof_mark(c, st, 3);
         bool in_b = false;
-        TRY(hsk_sort_passes(c, c->keys.p, c->alt.p, nullptr, nullptr, nk, kw, P,
-                            (uint64_t*)c->pass_hist.p, &in_b, st, false));
+        TRY(sort_segments(c, c->keys.p, c->alt.p, nullptr, nullptr, d_kbase, C, (uint32_t)max_kt, kw, P,
+                          (const uint64_t*)c->digit_off.p, &in_b, st));
         if (c->prof) c->prof_passes += P;
         prof_mark(c, st, 4);
         const void* sorted = in_b ? c->alt.p : c->keys.p;
         TRY(hsk_rle_chunk(c, sorted, nk, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
         prof_mark(c, st, 5);
     }
-    if (chunks.size() > 1)
+    if (total_segments > 1)
         TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st));
     prof_mark(c, st, 6);
     CK(cudaEventRecord(c->ev1, st));
@@ -835,17 +916,7 @@ extern "C" int hsk_stage_sort(hsk_ctx* c, uint64_t* d_keys, uint64_t n, int key_
     CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
     c->ctr_used = 0;
     if (n <= 1) return HSK_OK;
-    size_t kb = (size_t)key_words * 8;
-    int P = n_passes_for(key_bits);
-    TRY(hsk_ensure(c, c->alt, n * kb, false));
-    TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
-    TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
-    CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
-    launch_digit_hist(d_keys, key_words, n, (uint64_t*)c->pass_hist.p, P, c->num_sms * 4, st);
-    bool in_b = false;
-    TRY(hsk_sort_passes(c, d_keys, c->alt.p, nullptr, nullptr, n, key_words, P,
-                        (uint64_t*)c->pass_hist.p, &in_b, st));
-    if (in_b) CK(cudaMemcpyAsync(d_keys, c->alt.p, n * kb, cudaMemcpyDeviceToDevice, st));
+    TRY(plain_sort(c, d_keys, nullptr, n, key_words, key_bits, c->alt, nullptr, st));
     return read_device_error(c, st);
 }
 

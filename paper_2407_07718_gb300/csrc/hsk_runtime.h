@@ -19,6 +19,8 @@
 #define HSK_N_COUNTERS 1024
 #define HSK_SMALL_BYTES 8192
 #define HSK_MAX_BUCKETS 8192
+#define HSK_SEGMENTS 64             // bucket groups sorted side by side
+#define HSK_MIN_SEGMENT_KMERS 16384 // smaller jobs use fewer segments
 
 struct DevBuf {
     void* p = nullptr;
@@ -92,7 +94,7 @@ struct hsk_ctx {
     DevBuf in_reads, in_offsets;     // staged host inputs
     DevBuf pk, iv, rs;               // S1 packed bases, invalid mask, read-start mask
     DevBuf cta_cnt, cta_off, bucket_kmers, bucket_rec, records;  // S2/S3
-    DevBuf keys, alt, pass_hist, digit_off, lb_status;             // S4
+    DevBuf keys, alt, pass_hist, digit_off, lb_status, seg;        // S4
     DevBuf heads, out_keys, out_counts, hist;                      // S5
     DevBuf pair_alt_keys, pair_alt_counts;                         // S6
     DevBuf batch_a, batch_b, batch_c, batch_d;                     // batched form
@@ -114,7 +116,7 @@ struct hsk_ctx {
 
     std::vector<DevBuf*> all_bufs() {
         return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
-                &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &heads,
+                &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads,
                 &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &batch_a,
                 &batch_b, &batch_c, &batch_d};
     }

@@ -18,6 +18,7 @@ constexpr int RLE_TILE = 256 * RLE_ITEMS;
 constexpr int RLE_SBINS = 2048;  // histogram bins kept in shared memory
 
 uint64_t rle_tiles(uint64_t n, int /*key_words*/) { return (n + RLE_TILE - 1) / RLE_TILE; }
+uint64_t rle_status_words(uint64_t n) { return ((n + RLE_TILE - 1) / RLE_TILE + 1) * LB_PAD; }
 
 // Order-preserving compaction of one tile: flags[i] for item (i, thread) in
 // index order i * 256 + threadIdx.x.  Returns each thread's per-item output
@@ -72,9 +73,9 @@ __global__ void __launch_bounds__(256) k_rle_heads(const K* __restrict__ keys, u
         if (tile == 0) {
             st_relaxed(status, lb_word(LB_PREFIX, epoch, total));
         } else {
-            st_relaxed(status + tile, lb_word(LB_AGG, epoch, total));
-            pre = lookback_exclusive(status, 1, tile, epoch, err);
-            st_relaxed(status + tile, lb_word(LB_PREFIX, epoch, pre + total));
+            st_relaxed(status + tile * LB_PAD, lb_word(LB_AGG, epoch, total));
+            pre = lookback_exclusive_win<16>(status, LB_PAD, tile, epoch, err);
+            st_relaxed(status + tile * LB_PAD, lb_word(LB_PREFIX, epoch, pre + total));
         }
         s_prefix = pre;
         if (tile == n_tiles - 1) {
@@ -148,9 +149,9 @@ __global__ void __launch_bounds__(256) k_rle_emit(const K* __restrict__ keys, co
         if (tile == 0) {
             st_relaxed(status, lb_word(LB_PREFIX, epoch, total));
         } else {
-            st_relaxed(status + tile, lb_word(LB_AGG, epoch, total));
-            pre = lookback_exclusive(status, 1, tile, epoch, err);
-            st_relaxed(status + tile, lb_word(LB_PREFIX, epoch, pre + total));
+            st_relaxed(status + tile * LB_PAD, lb_word(LB_AGG, epoch, total));
+            pre = lookback_exclusive_win<16>(status, LB_PAD, tile, epoch, err);
+            st_relaxed(status + tile * LB_PAD, lb_word(LB_PREFIX, epoch, pre + total));
         }
         s_prefix = pre;
         if (tile == n_tiles - 1) *n_out = pre + total;

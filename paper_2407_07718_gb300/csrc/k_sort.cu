@@ -7,11 +7,21 @@
 // the tile's global digit offsets by decoupled look-back over earlier tiles
 // and scatters the tile, digit by digit, with contiguous writes.
 //
-//   k_expand      -- supermer records -> canonical keys, plus the up-front
-//                    digit histograms of all passes (fused: no extra read).
+// Segments.  The keys of a job are split into C segments, each a group of
+// minimizer buckets -- the paper's tasks (Sec. 3.4), which never share a
+// k-mer value -- and every segment is sorted on its own, as the paper's
+// workers sort their tasks.  All segments go through one launch per pass
+// with their tiles interleaved (global tile g is tile g / C of segment
+// g % C), so each segment's look-back chain holds only ~1/C of the tiles in
+// flight and a tile seldom waits for a predecessor that is itself still
+// looking back.  A plain sort is the case C = 1.
+//
+//   k_expand_seg  -- supermer records -> canonical keys of each segment, plus
+//                    the segment's up-front digit histograms (fused).
 //   k_digit_hist  -- up-front histograms of plain keys (stage sort, S6).
-//   k_onesweep    -- one 8-bit LSD pass; u64 keys (k <= 32) or 128-bit keys
-//                    (k <= 64), optionally carrying a uint32 value.
+//   k_digit_offsets_seg -- per (pass, segment) exclusive digit offsets.
+//   k_onesweep_seg -- one 8-bit LSD pass over all segments; u64 keys
+//                    (k <= 32) or 128-bit keys (k <= 64), optional uint32 value.
 #include "hsk_device.cuh"
 
 namespace hsk {
@@ -20,12 +30,12 @@ constexpr int RADIX = 256;
 constexpr int MAX_PASS = 16;
 
 // ---------------------------------------------------------------------------
-// supermer records -> keys (+ digit histograms)
+// supermer records -> keys (+ digit histograms), per segment
 // ---------------------------------------------------------------------------
 constexpr int EXP_RPT = 4;                 // records per thread
 constexpr int EXP_TILE = 256 * EXP_RPT;    // records per tile
 
-uint64_t expand_status_words(uint64_t n_rec) { return (n_rec + EXP_TILE - 1) / EXP_TILE + 1; }
+uint64_t expand_tiles(uint64_t n_rec) { return (n_rec + EXP_TILE - 1) / EXP_TILE; }
 int expand_grid(int num_sms) { return num_sms * 4; }
 
 __device__ __forceinline__ u64 sel4(const u64 (&W)[4], uint32_t i) {
@@ -55,23 +65,48 @@ __device__ __forceinline__ key128 record_kmer128(const u64 (&W)[4], uint32_t j, 
     return r;
 }
 
+// Each CTA starts on segment blockIdx.x % C and takes that segment's record
+// tiles from its counter; when they run out it flushes the segment's
+// histogram and moves on to the next segment, so CTAs finish together.
+// Segment c: records [rec_base[c], rec_base[c+1]), keys written from
+// key_base[c]; look-back status of its tiles at status + c * st_stride.
 template <bool WIDE>
-__global__ void __launch_bounds__(256) k_expand(const u64* __restrict__ rec, u64 n_rec, int rec_words,
-                                                int k, void* __restrict__ keys_out, u64 n_keys,
-                                                u64* status, uint32_t* tile_ctr, uint32_t epoch,
-                                                u64* __restrict__ hist, int n_pass, int* err) {
+__global__ void __launch_bounds__(256) k_expand_seg(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
+                                                    const u64* __restrict__ key_base, uint32_t C, int k,
+                                                    void* __restrict__ keys_out, u64* status, u64 st_stride,
+                                                    uint32_t* tile_ctr, uint32_t epoch, u64* __restrict__ hist,
+                                                    int n_pass, int* err) {
+    constexpr int RW = WIDE ? 4 : 2;
     __shared__ uint32_t s_hist[MAX_PASS * RADIX];
     __shared__ u64 s_scr[9];
     __shared__ u64 s_prefix;
     __shared__ uint32_t s_tile;
     for (int i = threadIdx.x; i < n_pass * RADIX; i += 256) s_hist[i] = 0;
-    const u64 n_tiles = (n_rec + EXP_TILE - 1) / EXP_TILE;
-    for (;;) {
+    uint32_t c = blockIdx.x % C, visited = 0;
+    bool dirty = false;
+    while (visited < C) {
         __syncthreads();
-        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr + c, 1u);
         __syncthreads();
         const u64 tile = s_tile;
-        if (tile >= n_tiles) break;
+        const u64 rb = rec_base[c], n_rec = rec_base[c + 1] - rb;
+        const u64 n_tiles = (n_rec + EXP_TILE - 1) / EXP_TILE;
+        if (tile >= n_tiles) {  // segment done: flush its histogram, move on
+            if (dirty) {
+                u64* h = hist + (u64)c * n_pass * RADIX;
+                for (int i = threadIdx.x; i < n_pass * RADIX; i += 256) {
+                    uint32_t v = s_hist[i];
+                    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(h + i), (unsigned long long)v);
+                    s_hist[i] = 0;
+                }
+                dirty = false;
+            }
+            c = c + 1 == C ? 0 : c + 1;
+            ++visited;
+            continue;
+        }
+        dirty = true;
+        u64* seg_status = status + (u64)c * st_stride;
         const u64 r0 = tile * EXP_TILE + (u64)threadIdx.x * EXP_RPT;
         u64 W[EXP_RPT][4];
         uint32_t nk[EXP_RPT];
@@ -81,7 +116,7 @@ __global__ void __launch_bounds__(256) k_expand(const u64* __restrict__ rec, u64
             nk[i] = 0;
             W[i][0] = W[i][1] = W[i][2] = W[i][3] = 0;
             if (r0 + i < n_rec) {
-                const u64* r = rec + (r0 + i) * (u64)rec_words;
+                const u64* r = rec + (rb + r0 + i) * (u64)RW;
                 ulonglong2 a = *reinterpret_cast<const ulonglong2*>(r);
                 W[i][0] = a.x;
                 W[i][1] = a.y;
@@ -99,24 +134,24 @@ __global__ void __launch_bounds__(256) k_expand(const u64* __restrict__ rec, u64
         if (threadIdx.x == 0) {
             u64 pre = 0;
             if (tile == 0) {
-                st_relaxed(status, lb_word(LB_PREFIX, epoch, total));
+                st_relaxed(seg_status, lb_word(LB_PREFIX, epoch, total));
             } else {
-                st_relaxed(status + tile, lb_word(LB_AGG, epoch, total));
-                pre = lookback_exclusive(status, 1, tile, epoch, err);
-                st_relaxed(status + tile, lb_word(LB_PREFIX, epoch, pre + total));
+                st_relaxed(seg_status + tile * LB_PAD, lb_word(LB_AGG, epoch, total));
+                pre = lookback_exclusive_win<16>(seg_status, LB_PAD, tile, epoch, err);
+                st_relaxed(seg_status + tile * LB_PAD, lb_word(LB_PREFIX, epoch, pre + total));
             }
             s_prefix = pre;
         }
         __syncthreads();
-        u64 o = s_prefix + excl;
-        if (o + sum > n_keys) {
+        u64 o = key_base[c] + s_prefix + excl;
+        if (o + sum > key_base[c + 1]) {
             raise_error(err, HSK_DERR_BOUNDS);
             continue;
         }
 #pragma unroll
         for (int i = 0; i < EXP_RPT; ++i) {
             // the record's low 8 bits of its last word hold n; they never fall
-            // inside a k-mer (n + k - 1 <= 32 * rec_words - 4 bases)
+            // inside a k-mer (n + k - 1 <= 32 * record words - 4 bases)
             for (uint32_t j = 0; j < nk[i]; ++j, ++o) {
                 if (!WIDE) {
                     u64 key = canonical64(record_kmer64(W[i], j, k), k);
@@ -132,28 +167,30 @@ __global__ void __launch_bounds__(256) k_expand(const u64* __restrict__ rec, u64
             }
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_pass * RADIX; i += 256)
-        if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(hist + i), (unsigned long long)s_hist[i]);
 }
 
-void launch_expand(const uint64_t* records, uint64_t n_rec, int rec_words, int k, void* keys,
-                   uint64_t n_keys, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch,
-                   uint64_t* hist, int n_pass, int* err, int grid, cudaStream_t st) {
-    if (n_rec == 0) return;
+void launch_expand_seg(const uint64_t* records, const uint64_t* rec_base, const uint64_t* key_base,
+                       uint32_t C, uint64_t max_tiles, int k, void* keys, uint64_t* status,
+                       uint32_t* tile_ctrs, uint32_t epoch, uint64_t* hist, int n_pass, int* err,
+                       int grid, cudaStream_t st) {
+    if (C == 0 || max_tiles == 0) return;
     count_launch();
-    uint64_t tiles = (n_rec + EXP_TILE - 1) / EXP_TILE;
-    unsigned g = (unsigned)(tiles < (uint64_t)grid ? tiles : (uint64_t)grid);
+    uint64_t want = (uint64_t)C * max_tiles;
+    unsigned g = (unsigned)(want < (uint64_t)grid ? want : (uint64_t)grid);
+    if (g < C) g = C;  // every segment gets a starting CTA
+    const u64 stride = (max_tiles + 1) * LB_PAD;
     if (k <= 32)
-        k_expand<false><<<g, 256, 0, st>>>((const u64*)records, n_rec, rec_words, k, keys, n_keys,
-                                           (u64*)status, tile_ctr, epoch, (u64*)hist, n_pass, err);
+        k_expand_seg<false><<<g, 256, 0, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)key_base, C,
+                                               k, keys, (u64*)status, stride, tile_ctrs, epoch, (u64*)hist,
+                                               n_pass, err);
     else
-        k_expand<true><<<g, 256, 0, st>>>((const u64*)records, n_rec, rec_words, k, keys, n_keys,
-                                          (u64*)status, tile_ctr, epoch, (u64*)hist, n_pass, err);
+        k_expand_seg<true><<<g, 256, 0, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)key_base, C,
+                                              k, keys, (u64*)status, stride, tile_ctrs, epoch, (u64*)hist,
+                                              n_pass, err);
 }
 
 // ---------------------------------------------------------------------------
-// up-front digit histograms of plain keys
+// up-front digit histograms of plain keys (one segment)
 // ---------------------------------------------------------------------------
 template <typename K>
 __global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, u64 n,
@@ -182,48 +219,62 @@ void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hi
         k_digit_hist<key128><<<g, 256, 0, st>>>((const key128*)keys, n, (u64*)hist, n_pass);
 }
 
-__global__ void __launch_bounds__(256) k_digit_offsets(const u64* __restrict__ hist, u64* __restrict__ off) {
+// doff[(p * C + c) * 256 + d] = key_base[c] + sum over d' < d of hist[(c * P + p) * 256 + d']
+__global__ void __launch_bounds__(256) k_digit_offsets_seg(const u64* __restrict__ hist, const u64* __restrict__ key_base,
+                                                           u64* __restrict__ doff, int n_pass, uint32_t C) {
     __shared__ u64 s_scr[9];
     const int p = blockIdx.x;
-    u64 v = hist[p * RADIX + threadIdx.x], total;
+    const uint32_t c = blockIdx.y;
+    u64 v = hist[((u64)c * n_pass + p) * RADIX + threadIdx.x], total;
     u64 e = block_excl_sum<256, u64>(v, s_scr, total);
-    off[p * RADIX + threadIdx.x] = e;
+    doff[((u64)p * C + c) * RADIX + threadIdx.x] = key_base[c] + e;
 }
 
-void launch_digit_offsets(const uint64_t* hist, uint64_t* digit_off, int n_pass, cudaStream_t st) {
-    if (n_pass <= 0) return;
+void launch_digit_offsets_seg(const uint64_t* hist, const uint64_t* key_base, uint64_t* doff, int n_pass,
+                              uint32_t C, cudaStream_t st) {
+    if (n_pass <= 0 || C == 0) return;
     count_launch();
-    k_digit_offsets<<<n_pass, 256, 0, st>>>((const u64*)hist, (u64*)digit_off);
+    k_digit_offsets_seg<<<dim3(n_pass, C), 256, 0, st>>>((const u64*)hist, (const u64*)key_base, (u64*)doff,
+                                                         n_pass, C);
 }
 
 // ---------------------------------------------------------------------------
-// one onesweep LSD pass
+// one onesweep LSD pass over all segments
 // ---------------------------------------------------------------------------
 template <typename K>
 struct PassCfg;
+#ifndef HSK_OS_ITEMS_U64
+#define HSK_OS_ITEMS_U64 16
+#endif
 template <>
 struct PassCfg<u64> {
-    static constexpr int ITEMS = 16;  // 4096 keys, 32 KB per tile
+    static constexpr int ITEMS = HSK_OS_ITEMS_U64;  // 16: 4096 keys, 32 KB per tile
 };
 template <>
 struct PassCfg<key128> {
     static constexpr int ITEMS = 8;   // 2048 keys, 32 KB per tile
 };
 
-uint64_t onesweep_tiles(uint64_t n, int key_words) {
-    uint64_t tile = 256ull * (key_words == 1 ? PassCfg<u64>::ITEMS : PassCfg<key128>::ITEMS);
-    return (n + tile - 1) / tile;
+uint64_t onesweep_tile_keys(int key_words) {
+    return 256ull * (key_words == 1 ? PassCfg<u64>::ITEMS : PassCfg<key128>::ITEMS);
 }
 
-template <typename K>
-__device__ __forceinline__ K load_key(const K* p) { return *p; }
+__device__ __forceinline__ u64 load_stream(const u64* p) { return __ldcs(reinterpret_cast<const unsigned long long*>(p)); }
+__device__ __forceinline__ key128 load_stream(const key128* p) {
+    ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(p));
+    return key128{v.x, v.y};
+}
 
+// Registers per thread are capped so that 4 CTAs of 256 threads fit an SM
+// (64 registers); ranks are kept as 16-bit halves (a tile holds < 65536 keys).
+// Segment c holds keys [key_base[c], key_base[c+1]) in both buffers; the
+// look-back word of digit d of tile j of segment c is status[(c*tmax + j)*256 + d].
 template <typename K, bool HAS_VAL>
-__global__ void __launch_bounds__(256) k_onesweep(const K* __restrict__ kin, K* __restrict__ kout,
-                                                  const uint32_t* __restrict__ vin,
-                                                  uint32_t* __restrict__ vout, u64 n, int shift,
-                                                  const u64* __restrict__ digit_off, u64* status,
-                                                  uint32_t* tile_ctr, uint32_t epoch, int* err) {
+__global__ void __launch_bounds__(256, HAS_VAL ? 3 : 4)
+    k_onesweep_seg(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
+                   uint32_t* __restrict__ vout, const u64* __restrict__ key_base, uint32_t C, uint32_t tmax,
+                   int shift, const u64* __restrict__ doff, u64* status, uint32_t* tile_ctr, uint32_t epoch,
+                   int* err) {
     constexpr int ITEMS = PassCfg<K>::ITEMS;
     constexpr int TILE = 256 * ITEMS;
     constexpr int WARPS = 8;
@@ -240,40 +291,46 @@ __global__ void __launch_bounds__(256) k_onesweep(const K* __restrict__ kin, K* 
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
     for (int i = threadIdx.x; i < WARPS * RADIX; i += 256) (&s_whist[0][0])[i] = 0;
     __syncthreads();
-    const u64 tile = s_tile;
-    const u64 base = tile * TILE;
+    const uint32_t g = s_tile;
+    const uint32_t c = g % C, tile = g / C;
+    const u64 sb = key_base[c], sn = key_base[c + 1] - sb;
+    if ((u64)tile * TILE >= sn) return;  // this segment has fewer tiles (uniform exit)
+    const u64 base = sb + (u64)tile * TILE;
+    const u64 seg_end = sb + sn;
     const u64 wbase = base + (u64)warp * (ITEMS * 32);
 
     K key[ITEMS];
-    uint32_t val[ITEMS];
-    uint32_t rank[ITEMS];
-    uint32_t dig[ITEMS];
+    uint32_t val[HAS_VAL ? ITEMS : 1];
+    uint32_t rank2[ITEMS / 2];  // two 16-bit in-warp ranks per register
+    // keys of this warp that exist (the last tile of a segment is partial)
+    const int wvalid = seg_end > wbase ? (int)(seg_end - wbase < (u64)(ITEMS * 32) ? seg_end - wbase : (u64)(ITEMS * 32)) : 0;
+    const K* wk = kin + wbase;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        u64 idx = wbase + i * 32 + lane;
-        bool ok = idx < n;
-        if (ok) {
-            key[i] = kin[idx];
-            if (HAS_VAL) val[i] = vin[idx];
+        if (i * 32 + lane < wvalid) {
+            key[i] = load_stream(wk + i * 32 + lane);
+            if (HAS_VAL) val[i] = __ldcs(vin + wbase + i * 32 + lane);
         } else {
             key[i] = K{};
-            val[i] = 0;
+            if (HAS_VAL) val[i] = 0;
         }
-        dig[i] = ok ? key_digit(key[i], shift, 0xFF) : RADIX;  // RADIX: padding
     }
     // ---- rank within the warp, in index order (stable) ----
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        uint32_t d = dig[i];
+        const bool ok = i * 32 + lane < wvalid;
+        uint32_t d = ok ? key_digit(key[i], shift, 0xFF) : RADIX;  // RADIX: padding
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t below = __popc(peers & lt);
         uint32_t cnt = __popc(peers);
-        uint32_t b = d < RADIX ? s_whist[warp][d] : 0u;
+        uint32_t b = ok ? s_whist[warp][d] : 0u;
         __syncwarp();
-        if (d < RADIX && below == 0) s_whist[warp][d] = b + cnt;
+        if (ok && below == 0) s_whist[warp][d] = b + cnt;
         __syncwarp();
-        rank[i] = b + below;
+        uint32_t r = b + below;
+        if (i & 1) rank2[i / 2] |= r << 16;
+        else rank2[i / 2] = r;
     }
     __syncthreads();
     // ---- per digit: exclusive offsets across warps, tile count ----
@@ -281,41 +338,47 @@ __global__ void __launch_bounds__(256) k_onesweep(const K* __restrict__ kin, K* 
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) {
-        uint32_t c = s_whist[w][d];
+        uint32_t cc = s_whist[w][d];
         s_whist[w][d] = cnt;
-        cnt += c;
+        cnt += cc;
     }
-    // publish this tile's count of digit d, then look back for its prefix
-    u64* my = status + tile * RADIX + d;
+    // publish this tile's count of digit d (its look-back comes after the keys
+    // have left the registers).  Status words are laid out [segment][tile]
+    // [digit]: a tile publishes its 256 words into 2 KB of its own, so tiles
+    // never contend for the same L2 sectors.
+    u64* seg_status = status + (u64)c * tmax * RADIX;
+    u64* my = seg_status + (u64)tile * RADIX + d;
     if (tile == 0) st_relaxed(my, lb_word(LB_PREFIX, epoch, cnt));
     else st_relaxed(my, lb_word(LB_AGG, epoch, cnt));
     uint32_t tot;
     uint32_t tstart = block_excl_sum<256, uint32_t>(cnt, s_scr, tot);
     s_tstart[d] = tstart;
-    u64 excl = 0;
-    if (tile > 0) {
-        excl = lookback_exclusive(status + d, RADIX, tile, epoch, err);
-        st_relaxed(my, lb_word(LB_PREFIX, epoch, excl + cnt));
-    }
-    s_gbase[d] = digit_off[d] + excl - tstart;
     __syncthreads();
     // ---- place keys in shared memory in tile-sorted order ----
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        uint32_t dd = dig[i];
-        if (dd < RADIX) {
-            uint32_t r = s_tstart[dd] + s_whist[warp][dd] + rank[i];
+        if (i * 32 + lane < wvalid) {
+            uint32_t dd = key_digit(key[i], shift, 0xFF);
+            uint32_t rr = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
+            uint32_t r = s_tstart[dd] + s_whist[warp][dd] + rr;
             s_keys[r] = key[i];
             if (HAS_VAL) s_vals[r] = val[i];
         }
     }
+    // ---- look back for the tile's offset of digit d within its segment ----
+    u64 excl = 0;
+    if (tile > 0) {
+        excl = lookback_exclusive_win<8>(seg_status + d, RADIX, tile, epoch, err);
+        st_relaxed(my, lb_word(LB_PREFIX, epoch, excl + cnt));
+    }
+    s_gbase[d] = doff[(u64)c * RADIX + d] + excl - tstart;
     __syncthreads();
     // ---- scatter: consecutive threads write consecutive slots of a digit ----
-    const uint32_t tile_n = (uint32_t)(n - base < (u64)TILE ? n - base : (u64)TILE);
+    const uint32_t tile_n = (uint32_t)(seg_end - base < (u64)TILE ? seg_end - base : (u64)TILE);
     for (uint32_t j = threadIdx.x; j < tile_n; j += 256) {
         K kk = s_keys[j];
         u64 pos = s_gbase[key_digit(kk, shift, 0xFF)] + j;
-        if (pos >= n) {  // only after a failed look-back: never write out of bounds
+        if (pos < sb || pos >= seg_end) {  // only after a failed look-back: never write out of bounds
             raise_error(err, HSK_DERR_BOUNDS);
             continue;
         }
@@ -325,30 +388,32 @@ __global__ void __launch_bounds__(256) k_onesweep(const K* __restrict__ kin, K* 
 }
 
 template <typename K, bool HV>
-static void launch_pass_t(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, uint64_t n,
-                          int shift, const uint64_t* digit_off, uint64_t* status, uint32_t* tile_ctr,
-                          uint32_t epoch, int* err, cudaStream_t st) {
+static void launch_pass_t(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, const uint64_t* key_base,
+                          uint32_t C, uint32_t tmax, int shift, const uint64_t* doff, uint64_t* status,
+                          uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st) {
     constexpr int TILE = 256 * PassCfg<K>::ITEMS;
     size_t smem = (size_t)TILE * sizeof(K) + (HV ? (size_t)TILE * sizeof(uint32_t) : 0);
-    auto fn = k_onesweep<K, HV>;
+    auto fn = k_onesweep_seg<K, HV>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    uint64_t tiles = (n + TILE - 1) / TILE;
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     count_launch();
-    fn<<<(unsigned)tiles, 256, smem, st>>>((const K*)kin, (K*)kout, vin, vout, n, shift,
-                                           (const u64*)digit_off, (u64*)status, tile_ctr, epoch, err);
+    fn<<<(unsigned)((uint64_t)C * tmax), 256, smem, st>>>((const K*)kin, (K*)kout, vin, vout, (const u64*)key_base,
+                                                          C, tmax, shift, (const u64*)doff, (u64*)status, tile_ctr,
+                                                          epoch, err);
 }
 
-void launch_onesweep(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, uint64_t n,
-                     int key_words, int shift, const uint64_t* digit_off, uint64_t* status,
-                     uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st) {
-    if (n == 0) return;
+void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
+                         const uint64_t* key_base, uint32_t C, uint32_t tmax, int key_words, int shift,
+                         const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err,
+                         cudaStream_t st) {
+    if (C == 0 || tmax == 0) return;
     bool hv = vin != nullptr;
     if (key_words == 1) {
-        if (hv) launch_pass_t<u64, true>(kin, kout, vin, vout, n, shift, digit_off, status, tile_ctr, epoch, err, st);
-        else launch_pass_t<u64, false>(kin, kout, vin, vout, n, shift, digit_off, status, tile_ctr, epoch, err, st);
+        if (hv) launch_pass_t<u64, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
+        else launch_pass_t<u64, false>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
     } else {
-        if (hv) launch_pass_t<key128, true>(kin, kout, vin, vout, n, shift, digit_off, status, tile_ctr, epoch, err, st);
-        else launch_pass_t<key128, false>(kin, kout, vin, vout, n, shift, digit_off, status, tile_ctr, epoch, err, st);
+        if (hv) launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
+        else launch_pass_t<key128, false>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
     }
 }
 

@@ -337,7 +337,7 @@ int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets) 
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = 256 * SCAN_ITEMS;
 
-uint64_t scan_status_words(uint64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+uint64_t scan_status_words(uint64_t n) { return ((n + SCAN_TILE - 1) / SCAN_TILE + 1) * LB_PAD; }
 
 __global__ void __launch_bounds__(256) k_scan_u32(const uint32_t* __restrict__ in, uint64_t n,
                                                   u64* __restrict__ out, u64* status,
@@ -363,9 +363,9 @@ __global__ void __launch_bounds__(256) k_scan_u32(const uint32_t* __restrict__ i
         if (tile == 0) {
             st_relaxed(status, lb_word(LB_PREFIX, epoch, total));
         } else {
-            st_relaxed(status + tile, lb_word(LB_AGG, epoch, total));
-            pre = lookback_exclusive(status, 1, tile, epoch, err);
-            st_relaxed(status + tile, lb_word(LB_PREFIX, epoch, pre + total));
+            st_relaxed(status + tile * LB_PAD, lb_word(LB_AGG, epoch, total));
+            pre = lookback_exclusive_win<16>(status, LB_PAD, tile, epoch, err);
+            st_relaxed(status + tile * LB_PAD, lb_word(LB_PREFIX, epoch, pre + total));
         }
         s_prefix = pre;
     }
