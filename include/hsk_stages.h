@@ -87,6 +87,28 @@ int hsk_stage_rle(hsk_ctx* ctx, const uint64_t* d_sorted, uint64_t n, int key_wo
 int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t n,
                     int key_words, int key_bits, void* stream);
 
+/* Stage S4's key sort for callers that cannot allocate device memory (the
+ * paper has no counterpart: this serves callers of this library, not the
+ * method).  Such callers are, for example, processes whose device memory is
+ * all reserved up front by another allocator (a framework's caching allocator,
+ * a fixed arena), or code that must not take the device-wide synchronization
+ * cudaMalloc/cudaFree can imply.  Sorts n keys of key_words words (1, or 2 as
+ * {lo, hi}) in place, ascending, on the low key_bits bits (the others must be
+ * zero), with the same result as hsk_stage_sort, and calls no allocating
+ * routine.  Its scratch is one fixed array of about 8.7 MB that every GPU
+ * loading this library holds until the process exits; n may be at most
+ * HSK_NOALLOC_MAX_KEYS_U64 (key_words = 1) or HSK_NOALLOC_MAX_KEYS_U128
+ * (key_words = 2), larger n returns HSK_EOVERFLOW and does nothing.  The
+ * first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU (other streams, other host
+ * threads) race.  No context is needed; the work is ordered on `stream` and
+ * complete on return.  HSK_EINVAL for bad arguments, HSK_ECUDA / HSK_ETIMEOUT
+ * as elsewhere. */
+#define HSK_NOALLOC_MAX_KEYS_U64 (1u << 20)
+#define HSK_NOALLOC_MAX_KEYS_U128 (1u << 19)
+int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words, int key_bits, void* stream);
+
 /* Test hooks.  hsk_debug_fail_alloc_after(ctx, n): the n-th following device
  * allocation of the context fails as if the budget were exhausted (-1 turns
  * this off), to check that every caller returns HSK_ENOMEM cleanly.

@@ -95,6 +95,7 @@ def load():
             "hsk_profile_enable": ([P, i32], i32),
             "hsk_profile_read": ([P, C.POINTER(d), C.POINTER(u64), i32], i32),
             "hsk_launch_count": ([], u64),
+            "hsk_sort_keys_noalloc": ([P, u64, i32, i32, P], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -127,6 +128,16 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+NOALLOC_MAX_KEYS = {1: 1 << 20, 2: 1 << 19}
+
+
+def sort_keys_noalloc(keys_t, n: int, key_words: int, key_bits: int, stream=None) -> int:
+    """Sort n keys of a device tensor in place without any device allocation
+    (for callers that cannot allocate; see hsk_sort_keys_noalloc in
+    include/hsk_stages.h).  Returns the library's status code."""
+    return int(load().hsk_sort_keys_noalloc(_tptr(keys_t), n, key_words, key_bits, _stream_ptr(stream)))
 
 
 @dataclass
