@@ -34,9 +34,10 @@ _LIB = os.path.join(_HERE, "libhsk_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# Seed XOR-ed into each canonical m-mer before the finalizer (fmix64(0) = 0
-# would otherwise always make poly-A the minimizer).  Passed explicitly to both
-# the oracle and the library; counts never depend on it.
+# Seed XOR-ed into each folded canonical m-mer before the finalizer (its low
+# 32 bits are used; fmix32(0) = 0 would otherwise always make poly-A the
+# minimizer).  Passed explicitly to both the oracle and the library; counts
+# never depend on it.
 DEFAULT_SEED = 0x9E3779B97F4A7C15
 
 
@@ -86,6 +87,8 @@ def _load():
             lib.oracle_sort_u64.argtypes = [P, u64]
             lib.oracle_fmix64.argtypes = [u64]
             lib.oracle_fmix64.restype = u64
+            lib.oracle_fmix32.argtypes = [u32]
+            lib.oracle_fmix32.restype = u32
             _lib = lib
     return _lib
 
@@ -215,3 +218,7 @@ def sort_u64(keys: np.ndarray) -> np.ndarray:
 
 def fmix64(x: int) -> int:
     return int(_load().oracle_fmix64(x))
+
+
+def fmix32(x: int) -> int:
+    return int(_load().oracle_fmix32(x))

@@ -28,8 +28,9 @@
 //   upper-case A/C/G/T breaks the window; the histogram counts every distinct
 //   k-mer before the filter, with bin H-1 collecting counts >= H-1; the filter
 //   is inclusive [lo, hi]; output is in ascending key order; the m-mer score is
-//   MurmurHash3's 64-bit finalizer applied to (canonical m-mer XOR seed); the
-//   bucket of a window is minhash mod B, the remainder rule of Sec. 3.2.
+//   MurmurHash3's 32-bit finalizer applied to (low 32 bits XOR high 32 bits of
+//   the canonical m-mer, XOR the low 32 bits of the seed); the bucket of a
+//   window is minhash mod B, the remainder rule of Sec. 3.2.
 
 #include <algorithm>
 #include <cstdint>
@@ -98,8 +99,21 @@ static uint64_t fmix64(uint64_t h) {
     return h;
 }
 
+// MurmurHash3 32-bit finalizer ("fmix32", A. Appleby, public domain).
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Score of an m-mer (Sec. 3.2: a hash value; the lowest score is the
+// minimizer): fmix32 of the canonical code folded to 32 bits, XOR the seed.
 static uint64_t mmer_score(const char* s, int m, uint64_t seed) {
-    return fmix64((uint64_t)canonical_code(s, m) ^ seed);
+    uint64_t c = (uint64_t)canonical_code(s, m);
+    return fmix32((uint32_t)c ^ (uint32_t)(c >> 32) ^ (uint32_t)seed);
 }
 
 // Target of a minimizer (Sec. 3.2): the remainder of its hash value divided
@@ -368,7 +382,8 @@ uint64_t oracle_supermers(const char* reads, const uint64_t* offsets, uint64_t n
 // Stage reference for the sort alone: std::sort (Sec. 3.1).
 void oracle_sort_u64(uint64_t* keys, uint64_t n) { std::sort(keys, keys + n); }
 
-// fmix64 exposed for the known-answer test of the score function.
+// The finalizers exposed for the tests that pin the score function.
 uint64_t oracle_fmix64(uint64_t h) { return fmix64(h); }
+uint32_t oracle_fmix32(uint32_t h) { return fmix32(h); }
 
 }  // extern "C"

@@ -221,7 +221,33 @@ def test_score_function_is_the_murmur3_finalizer():
         assert inverse(oracle.fmix64(x)) == x
 
 
-@pytest.mark.parametrize("k,m", [(5, 2), (9, 4), (21, 11), (31, 17), (31, 31), (40, 1), (55, 21)])
+def test_score_finalizer_fmix32_is_the_murmur3_one():
+    """fmix32 is a bijection whose inverse uses the modular inverses of its two
+    published multipliers; a wrong constant or shift breaks the round trip."""
+    M = (1 << 32) - 1
+    i1, i2 = pow(0x85EBCA6B, -1, 1 << 32), pow(0xC2B2AE35, -1, 1 << 32)
+
+    def inverse(h):
+        h ^= h >> 16                      # undo h ^= h >> 16
+        h = (h * i2) & M
+        h ^= (h >> 13) ^ (h >> 26)        # undo h ^= h >> 13
+        h = (h * i1) & M
+        return h ^ (h >> 16)
+
+    assert oracle.fmix32(0) == 0
+    rng = np.random.default_rng(2)
+    for x in [1, 2, 3, 0xDEADBEEF, M] + [int(v) for v in rng.integers(0, 2**32, 200, dtype=np.uint64)]:
+        assert inverse(oracle.fmix32(x)) == x
+
+
+def score(mmer: str, seed: int) -> int:
+    """m-mer score written from its definition: fmix32 of the canonical code
+    folded to 32 bits, XOR the seed's low 32 bits."""
+    c = to_int(canonical_str(mmer))
+    return oracle.fmix32(((c & 0xFFFFFFFF) ^ (c >> 32) ^ seed) & 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("k,m", [(5, 2), (9, 4), (21, 11), (31, 17), (31, 31), (40, 1), (55, 21), (64, 32)])
 def test_deque_minimizer_matches_window_minimum(k, m):
     reads, offs = datagen.random_reads(k * 7 + m, 60, 0, 150, p_invalid=0.01)
     strs = strs_of(reads, offs)
@@ -233,7 +259,7 @@ def test_deque_minimizer_matches_window_minimum(k, m):
             w = s[i:i + k]
             if not all(ch in "ACGT" for ch in w):
                 continue
-            scores = [oracle.fmix64(to_int(canonical_str(w[j:j + m])) ^ seed) for j in range(k - m + 1)]
+            scores = [score(w[j:j + m], seed) for j in range(k - m + 1)]
             best = min(scores)
             last = max(j for j in range(len(scores)) if scores[j] == best)  # right-most tie
             want.append((int(offs[r]) + i, to_int(canonical_str(w)), best, int(offs[r]) + i + last))
