@@ -27,7 +27,7 @@ void launch_mark_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t n_ba
                         uint64_t* start_mask, int* err, cudaStream_t st);
 
 // ---- S2/S3 canonical k-mers, minimizers, supermers -------------------------
-enum { SM_COUNT = 0, SM_SCATTER = 1, SM_DUMP = 2 };
+enum { SM_DESC = 0, SM_DUMP = 2 };
 
 struct SmParams {
     const uint64_t* packed;
@@ -36,17 +36,18 @@ struct SmParams {
     uint64_t n_bases;
     uint64_t n_packed_words, n_mask_words;
     int k, m, w;
-    uint64_t seed;
-    uint32_t n_buckets;
-    int nmax;          // k-mers per supermer record at most
-    int rec_words;     // 2 (k <= 32) or 4 (k <= 64)
-    uint32_t grid;     // CTAs of the count and scatter launches (must match)
-    uint32_t* cta_counts;     // [n_buckets][grid] records per (bucket, CTA)      (count)
-    uint64_t* bucket_kmers;   // [n_buckets] k-mers per bucket (atomic adds)      (count)
-    const uint64_t* cta_off;  // [n_buckets][grid] first record slot             (scatter)
-    uint64_t* records;        // record array                                     (scatter)
-    uint64_t n_records_cap;
-    uint8_t* dump_valid;      // (dump)
+    uint32_t seed32;
+    uint32_t n_buckets;       // a power of two
+    int nmax;                 // k-mers per supermer record at most
+    uint32_t nmax_magic;      // ceil(2^32 / nmax): q = umulhi(x, magic) = x / nmax for x < 2^24
+    int rec_words;            // 2 (k <= 32) or 4 (k <= 64)
+    uint32_t grid;
+    uint64_t* desc;                    // supermer descriptors (DESC)
+    uint64_t desc_cap;
+    unsigned long long* desc_count;    // descriptors produced (may exceed desc_cap)
+    uint32_t* bucket_rec;              // [n_buckets] records per bucket (atomic adds)
+    uint64_t* bucket_kmers;            // [n_buckets] k-mers per bucket (atomic adds)
+    uint8_t* dump_valid;               // (DUMP)
     uint64_t* dump_key;
     uint64_t* dump_minhash;
     int* err;
@@ -55,13 +56,14 @@ struct SmParams {
 size_t supermer_smem_bytes(int mode, uint32_t n_buckets);
 int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets);
 void launch_supermer(int mode, const SmParams& p, cudaStream_t st);
+// records from descriptors: bucket_off[B+1] record offsets, cursor[B] zeroed
+void launch_scatter_desc(const uint64_t* desc, uint64_t n_desc, const uint64_t* packed, int k,
+                         const uint64_t* bucket_off, uint32_t* cursor, uint64_t* records, uint64_t n_records,
+                         int* err, int grid, cudaStream_t st);
 
 // exclusive scan of n uint32 counts into uint64 offsets; offsets[n] = total.
 // Scratch: scan_status_words(n) uint64 words.
 uint64_t scan_status_words(uint64_t n);
-// out[b] = off[b * stride] for b in [0, B]; off[B * stride] is the total
-void launch_gather_stride(const uint64_t* off, uint32_t B, uint32_t stride, uint64_t* out,
-                          cudaStream_t st);
 void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* status,
                      uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st);
 

@@ -186,6 +186,7 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
     c->d_max = (uint32_t*)(s + 8);
     c->d_nheads = (uint64_t*)(s + 16);
     c->d_nout = (uint64_t*)(s + 24);
+    c->d_ndesc = (uint64_t*)(s + 32);
     c->counters = (uint32_t*)(s + 256);
     *out = c;
     return HSK_OK;
@@ -359,11 +360,12 @@ static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t 
     P.k = k;
     P.m = m;
     P.w = k - m + 1;
-    P.seed = c->cfg.seed;
+    P.seed32 = (uint32_t)c->cfg.seed;
     P.n_buckets = B;
     P.rec_words = k <= 32 ? 2 : 4;
     P.nmax = (P.rec_words * 32 - 4) - k + 1;  // bases per record minus (k - 1)
     if (P.nmax > 255) P.nmax = 255;
+    P.nmax_magic = (uint32_t)(((1ull << 32) + P.nmax - 1) / P.nmax);
     P.err = c->d_err;
 }
 
@@ -374,31 +376,43 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
     fill_sm_params(c, E, k, m, B, P);
     const bool wide = k > 32;
     const int nreg = P.w <= 33 ? 2 : 3;
-    int occ = std::min(supermer_max_ctas_per_sm(SM_SCATTER, wide, nreg, B),
-                       supermer_max_ctas_per_sm(SM_COUNT, wide, nreg, B));
-    uint64_t warp_tiles = (E.n_bases + 1023) / 1024;
+    const int occ = supermer_max_ctas_per_sm(SM_DESC, wide, nreg, B);
+    const uint64_t warp_tiles = (E.n_bases + 1023) / 1024;
     uint64_t g = std::min<uint64_t>((uint64_t)c->num_sms * occ, (warp_tiles + 7) / 8);
-    if (g == 0) g = 1;
-    P.grid = (uint32_t)g;
-    uint64_t nc = (uint64_t)B * g;
-    TRY(hsk_ensure(c, c->cta_cnt, nc * 4, false));
-    TRY(hsk_ensure(c, c->cta_off, (nc + 1) * 8, false));
+    P.grid = (uint32_t)std::max<uint64_t>(g, 1);
     TRY(hsk_ensure(c, c->bucket_kmers, (uint64_t)B * 8, false));
     TRY(hsk_ensure(c, c->bucket_rec, ((uint64_t)B + 1) * 8, false));
-    CK(cudaMemsetAsync(c->bucket_kmers.p, 0, (size_t)B * 8, st));
-    CK(cudaMemsetAsync(c->cta_cnt.p, 0, nc * 4, st));  // stays zero when there is no base
-    P.cta_counts = (uint32_t*)c->cta_cnt.p;
-    P.bucket_kmers = (uint64_t*)c->bucket_kmers.p;
-    launch_supermer(SM_COUNT, P, st);
-    CK(cudaGetLastError());
-    // exclusive scan over (bucket-major, CTA-minor) counts
-    TRY(ensure_status(c, scan_status_words(nc), st));
+    TRY(hsk_ensure(c, c->cta_cnt, (uint64_t)B * 4 * 2, false));  // records per bucket, then cursors
+    uint32_t* d_rec_cnt = (uint32_t*)c->cta_cnt.p;
+    uint32_t* d_cursor = d_rec_cnt + B;
+    // descriptors: about 2/(w+1) supermers per window (random minimizers), plus
+    // cuts at invalid bases, tile ends and the record cap; re-run if short
+    uint64_t cap = std::min<uint64_t>(E.n_bases + 1, (uint64_t)((double)E.n_bases *
+                                       (3.0 / (P.w + 1) + 1.0 / P.nmax + 1.0 / 256)) + (1u << 16));
+    uint64_t n_desc = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        TRY(hsk_ensure(c, c->cta_off, cap * 8, false));
+        CK(cudaMemsetAsync(c->bucket_kmers.p, 0, (size_t)B * 8, st));
+        CK(cudaMemsetAsync(d_rec_cnt, 0, (size_t)B * 4 * 2, st));
+        CK(cudaMemsetAsync(c->d_ndesc, 0, 8, st));
+        P.desc = (uint64_t*)c->cta_off.p;
+        P.desc_cap = cap;
+        P.desc_count = (unsigned long long*)c->d_ndesc;
+        P.bucket_rec = d_rec_cnt;
+        P.bucket_kmers = (uint64_t*)c->bucket_kmers.p;
+        launch_supermer(SM_DESC, P, st);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&n_desc, c->d_ndesc, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (n_desc <= cap) break;
+        cap = n_desc;  // the walk counted every supermer: one more run fits them all
+    }
+    // record offsets of the buckets
+    TRY(ensure_status(c, scan_status_words(B), st));
     uint32_t ep, *ctr;
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
-    launch_scan_u32((const uint32_t*)c->cta_cnt.p, nc, (uint64_t*)c->cta_off.p,
-                    (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
-    launch_gather_stride((const uint64_t*)c->cta_off.p, B, (uint32_t)g, (uint64_t*)c->bucket_rec.p, st);
+    launch_scan_u32(d_rec_cnt, B, (uint64_t*)c->bucket_rec.p, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
     CK(cudaGetLastError());
     // bucket statistics to the host (needed to size records and plan chunks)
     S.B = B;
@@ -408,16 +422,19 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
     CK(cudaMemcpyAsync(S.h_bucket_rec.data(), c->bucket_rec.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, st));
     TRY(read_device_error(c, st));
     S.n_records = S.h_bucket_rec[B];
+    if (S.n_records != n_desc) {
+        hsk_set_error(c, "supermer count mismatch: %llu descriptors, %llu records",
+                      (unsigned long long)n_desc, (unsigned long long)S.n_records);
+        return HSK_ECUDA;
+    }
     S.n_kmers = 0;
     for (uint64_t v : S.h_bucket_kmers) S.n_kmers += v;
     S.rec_words = P.rec_words;
     S.nmax = P.nmax;
     TRY(hsk_ensure(c, c->records, std::max<uint64_t>(S.n_records, 1) * P.rec_words * 8, false));
     prof_mark(c, st, 1);
-    P.cta_off = (const uint64_t*)c->cta_off.p;
-    P.records = (uint64_t*)c->records.p;
-    P.n_records_cap = S.n_records;
-    launch_supermer(SM_SCATTER, P, st);
+    launch_scatter_desc((const uint64_t*)c->cta_off.p, n_desc, E.packed, k, (const uint64_t*)c->bucket_rec.p,
+                        d_cursor, (uint64_t*)c->records.p, S.n_records, c->d_err, c->num_sms * 8, st);
     CK(cudaGetLastError());
     S.records = (const uint64_t*)c->records.p;
     return HSK_OK;
@@ -622,6 +639,10 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
                   DevResult& R) {
     memset(&R, 0, sizeof(R));
     c->zst = st;
+    if (n_bases >= (1ull << 40)) {
+        hsk_set_error(c, "n_bases %llu exceeds 2^40", (unsigned long long)n_bases);
+        return HSK_EOVERFLOW;
+    }
     const int kw = k <= 32 ? 1 : 2;
     const size_t kb = (size_t)kw * 8;
     const uint32_t H = c->cfg.hist_len;

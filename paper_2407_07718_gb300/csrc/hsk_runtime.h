@@ -86,6 +86,7 @@ struct hsk_ctx {
     uint32_t* d_max = nullptr;
     uint64_t* d_nheads = nullptr;
     uint64_t* d_nout = nullptr;
+    uint64_t* d_ndesc = nullptr;
     uint32_t* counters = nullptr;
     uint32_t ctr_used = 0;
     uint32_t epoch = 0;

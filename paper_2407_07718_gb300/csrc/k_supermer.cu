@@ -1,14 +1,14 @@
 // k_supermer.cu -- stages S2 and S3: canonical k-mers, hash-scored minimizers
 // and supermers scattered into minimizer-hashed buckets.
 //
-// Sec. 3.2: every m-mer is scored by a hash (here MurmurHash3's fmix64 of the
-// canonical m-mer XOR a seed); a k-mer's minimizer is its lowest-scoring
-// m-mer, and the same hash value decides the k-mer's target: bucket
-// score mod B (B a power of two).  Sec. 2.4: consecutive k-mers with the same target
-// form a supermer whose overlapping bases are stored once.  Sec. 3.4: the
-// buckets are the paper's tasks -- a k-mer value never lands in two of them,
-// because canonical m-mers give a k-mer and its reverse complement the same
-// minimizer score.
+// Sec. 3.2: every m-mer is scored by a hash (MurmurHash3's 32-bit finalizer
+// of the canonical m-mer folded to 32 bits, XOR a seed); a k-mer's minimizer
+// is its lowest-scoring m-mer, and the same hash value decides the k-mer's
+// target: bucket = score mod B (B a power of two).  Sec. 2.4: consecutive
+// k-mers with the same target form a supermer whose overlapping bases are
+// stored once.  Sec. 3.4: the buckets are the paper's tasks -- a k-mer value
+// never lands in two of them, because canonical m-mers give a k-mer and its
+// reverse complement the same minimizer score.
 //
 // GPU design (replaces the paper's per-read monotone deque): a warp walks a
 // tile of 1024 consecutive window starts in 32 steps, lane l handling window
@@ -17,10 +17,13 @@
 // the window minimum over w = k-m+1 scores comes from a log-step doubling of
 // minima across lanes with shuffles (a sparse table in registers).  Supermer
 // cuts (bucket change, invalid window, cap of nmax k-mers, tile end) come
-// from a warp max-scan of run starts.  The same walk runs three times:
-// COUNT (records per bucket and CTA, k-mers per bucket), SCATTER (write
-// records at scanned offsets; per-CTA shared-memory cursors, no global
-// atomics) and DUMP (per-window key and score, for the stage test).
+// from a warp max-scan of run starts.  The walk runs once (DESC): every
+// supermer becomes an 8-byte descriptor (start base, k-mer count, bucket),
+// buffered per warp in shared memory and appended to a global list with one
+// atomic per buffer; per-bucket record and k-mer counts are kept in shared
+// memory.  A second, light kernel scatters records into their buckets from
+// the descriptors.  DUMP mode writes per-window keys and scores for the stage
+// test.
 #include "hsk_device.cuh"
 
 namespace hsk {
@@ -30,58 +33,65 @@ constexpr int SM_STEPS = 32;
 constexpr int SM_TW = 32 * SM_STEPS;      // windows per warp tile
 constexpr int SM_PW = SM_TW / 32 + 6;     // packed words staged per warp (even)
 constexpr int SM_MW = SM_TW / 64 + 4;     // mask words staged per warp (even)
+constexpr int SM_DBUF = 128;              // descriptors buffered per warp
 
 size_t supermer_smem_bytes(int mode, uint32_t n_buckets) {
     size_t s = (size_t)SM_WARPS * (SM_PW + 2 * SM_MW) * sizeof(u64);
-    if (mode == SM_COUNT) s += (size_t)n_buckets * 2 * sizeof(uint32_t);
-    if (mode == SM_SCATTER) s += (size_t)n_buckets * (sizeof(u64) + sizeof(uint32_t));
+    if (mode == SM_DESC) s += (size_t)SM_WARPS * SM_DBUF * sizeof(u64) + (size_t)n_buckets * 2 * sizeof(uint32_t);
     return s;
 }
 
+// MurmurHash3's 32-bit finalizer (A. Appleby, public domain).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
 // Score of the m-mer at local base q of the staged words.
-__device__ __forceinline__ u64 mmer_score(const u64* pk, int q, int m, u64 seed) {
+__device__ __forceinline__ uint32_t mmer_score(const u64* pk, int q, int m, uint32_t seed) {
     u64 f = extract_k64(pk, (u64)q, m);
     u64 r = revcomp64(f, m);
-    return fmix64((f < r ? f : r) ^ seed);
+    u64 c = f < r ? f : r;
+    return fmix32((uint32_t)c ^ (uint32_t)(c >> 32) ^ seed);
 }
 
 // Value at index lane + d (0 <= d < 32) of the 32*NREG-long sequence held as
 // A[0..NREG) (A[r] holds indices 32r .. 32r+31), starting from register r.
 template <int NREG>
-__device__ __forceinline__ u64 seq_at(const u64 (&A)[NREG], int r, int d, int lane) {
+__device__ __forceinline__ uint32_t seq_at(const uint32_t (&A)[NREG], int r, int d, int lane) {
     int src = (lane + d) & 31;
-    u64 a = __shfl_sync(0xffffffffu, A[r], src);
-    u64 b = ~0ULL;
+    uint32_t a = __shfl_sync(0xffffffffu, A[r], src);
+    uint32_t b = 0xffffffffu;
     if (r + 1 < NREG) b = __shfl_sync(0xffffffffu, A[r + 1], src);
     return lane + d < 32 ? a : b;
 }
 
 // min(X[lane .. lane + w - 1]) with X given as NREG registers, w <= 32*NREG - 31.
 template <int NREG>
-__device__ __forceinline__ u64 window_min(const u64 (&X)[NREG], int w, int lane) {
-    u64 A[NREG];
+__device__ __forceinline__ uint32_t window_min(const uint32_t (&X)[NREG], int w, int lane) {
+    uint32_t A[NREG];
 #pragma unroll
     for (int r = 0; r < NREG; ++r) A[r] = X[r];
     int width = 1;
     while (2 * width <= w) {
         if (width == 32) {
 #pragma unroll
-            for (int r = 0; r < NREG; ++r) {
-                u64 nx = r + 1 < NREG ? A[r + 1] : ~0ULL;
-                A[r] = A[r] < nx ? A[r] : nx;
-            }
+            for (int r = 0; r < NREG; ++r) A[r] = min(A[r], r + 1 < NREG ? A[r + 1] : 0xffffffffu);
         } else {
-            u64 nx[NREG];
+            uint32_t nx[NREG];
 #pragma unroll
             for (int r = 0; r < NREG; ++r) nx[r] = seq_at<NREG>(A, r, width, lane);
 #pragma unroll
-            for (int r = 0; r < NREG; ++r) A[r] = A[r] < nx[r] ? A[r] : nx[r];
+            for (int r = 0; r < NREG; ++r) A[r] = min(A[r], nx[r]);
         }
         width *= 2;
     }
     int d = w - width;  // 0 <= d < width <= 32 (d < 32 because w <= 64)
-    u64 o = d == 0 ? A[0] : seq_at<NREG>(A, 0, d, lane);
-    return A[0] < o ? A[0] : o;
+    return d == 0 ? A[0] : min(A[0], seq_at<NREG>(A, 0, d, lane));
 }
 
 __device__ __forceinline__ int warp_incl_max(int v) {
@@ -101,36 +111,48 @@ __device__ __forceinline__ u64 keep_bases(u64 x, int nb) {
     return x & (~0ULL << (64 - 2 * nb));
 }
 
+// Descriptor of a supermer: start base (40 bits), k-mers (8 bits), bucket (16 bits).
+__device__ __forceinline__ u64 make_desc(u64 pos, uint32_t n, uint32_t b) {
+    return pos | ((u64)n << 40) | ((u64)b << 48);
+}
+
 template <int MODE, bool WIDE, int NREG>
 __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     u64* s_pk = reinterpret_cast<u64*>(smem);
     u64* s_iv = s_pk + SM_WARPS * SM_PW;
     u64* s_rs = s_iv + SM_WARPS * SM_MW;
-    unsigned char* s_b = reinterpret_cast<unsigned char*>(s_rs + SM_WARPS * SM_MW);
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_b);           // COUNT
-    uint32_t* s_km = s_cnt + P.n_buckets;                          // COUNT
-    u64* s_base = reinterpret_cast<u64*>(s_b);                     // SCATTER
-    uint32_t* s_cur = reinterpret_cast<uint32_t*>(s_base + P.n_buckets);  // SCATTER
+    u64* s_desc = s_rs + SM_WARPS * SM_MW;                                       // DESC
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_desc + SM_WARPS * SM_DBUF);  // DESC
+    uint32_t* s_km = s_cnt + P.n_buckets;                                        // DESC
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t B = P.n_buckets;
     const int k = P.k, m = P.m, w = P.w, nmax = P.nmax;
 
-    if (MODE == SM_COUNT) {
+    if (MODE == SM_DESC) {
         for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) s_cnt[b] = s_km[b] = 0;
-    } else if (MODE == SM_SCATTER) {
-        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-            s_base[b] = P.cta_off[(u64)b * P.grid + blockIdx.x];
-            s_cur[b] = 0;
-        }
+        __syncthreads();
     }
-    __syncthreads();
 
     u64* wpk = s_pk + warp * SM_PW;
     u64* wiv = s_iv + warp * SM_MW;
     u64* wrs = s_rs + warp * SM_MW;
+    u64* wdesc = s_desc + warp * SM_DBUF;
+    int nbuf = 0;  // descriptors buffered by this warp (warp-uniform)
     const u64 n_tiles = (P.n_bases + SM_TW - 1) / SM_TW;
+
+    // append the buffered descriptors to the global list (one atomic per flush)
+    auto flush = [&]() {
+        if (nbuf == 0) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.desc_count, (unsigned long long)nbuf);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < nbuf; i += 32)
+            if (base + i < P.desc_cap) P.desc[base + i] = wdesc[i];
+        __syncwarp();
+        nbuf = 0;
+    };
 
     for (u64 t = (u64)blockIdx.x * SM_WARPS + warp; t < n_tiles; t += (u64)gridDim.x * SM_WARPS) {
         const u64 p0 = t * SM_TW;
@@ -164,44 +186,31 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
         }
 
         // rolling m-mer scores: X[r] = score at local base 32*(s + r) + lane
-        u64 X[NREG];
+        uint32_t X[NREG];
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) X[r] = mmer_score(wpk, 32 * r + lane, m, P.seed);
+        for (int r = 0; r < NREG; ++r) X[r] = mmer_score(wpk, 32 * r + lane, m, P.seed32);
 
         int c_valid = 0, c_runstart = -1;   // carry from lane 31 of the previous step
         uint32_t c_b = 0;
         int pv = 0, pstart = 0, plp = 0, psm = 0;  // previous step, for delayed emission
         uint32_t pb = 0;
 
-        auto emit = [&](uint32_t b, int sm_start, int lp_end) {
-            int n = lp_end - sm_start + 1;
-            if (MODE == SM_COUNT) {
-                atomicAdd(&s_cnt[b], 1u);
-                atomicAdd(&s_km[b], (uint32_t)n);
-            } else if (MODE == SM_SCATTER) {
-                u64 slot = s_base[b] + atomicAdd(&s_cur[b], 1u);
-                if (slot >= P.n_records_cap) {
-                    raise_error(P.err, HSK_DERR_BOUNDS);
-                    return;
-                }
-                int nb = n + k - 1;  // bases in the record
-                u64* dst = reinterpret_cast<u64*>(P.records) + slot * (u64)P.rec_words;
-                if (!WIDE) {
-                    u64 a = extract_k64(wpk, (u64)sm_start, 32);
-                    u64 c = extract_k64(wpk, (u64)(sm_start + 32), 32);
-                    a = keep_bases(a, nb);
-                    c = keep_bases(c, nb - 32) | (u64)n;
-                    *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(a, c);
-                } else {
-                    u64 r[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        r[i] = keep_bases(extract_k64(wpk, (u64)(sm_start + 32 * i), 32), nb - 32 * i);
-                    r[3] |= (u64)n;
-                    reinterpret_cast<ulonglong2*>(dst)[0] = make_ulonglong2(r[0], r[1]);
-                    reinterpret_cast<ulonglong2*>(dst)[1] = make_ulonglong2(r[2], r[3]);
-                }
+        // emit the supermers that end in the previous step (end = valid and the
+        // next window is invalid or starts a new supermer)
+        auto emit_prev = [&](int nv, int ns) {
+            const bool end = pv && (!nv || ns);
+            const uint32_t ends = __ballot_sync(0xffffffffu, end);
+            if (!ends) return;
+            const int cnt = __popc(ends);
+            if (nbuf + cnt > SM_DBUF) flush();
+            if (end) {
+                const int n = plp - psm + 1;
+                atomicAdd(&s_cnt[pb], 1u);
+                atomicAdd(&s_km[pb], (uint32_t)n);
+                wdesc[nbuf + __popc(ends & ((1u << lane) - 1u))] = make_desc(p0 + psm, (uint32_t)n, pb);
             }
+            nbuf += cnt;
+            __syncwarp();
         };
 
         for (int s = 0; s < SM_STEPS; ++s) {
@@ -209,8 +218,8 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
             const u64 p = p0 + lp;
             int valid = (p + k <= P.n_bases) && mask_bits(wiv, lp, k) == 0 &&
                         (k == 1 || mask_bits(wrs, lp + 1, k - 1) == 0);
-            const u64 mh = window_min<NREG>(X, w, lane);
-            const uint32_t b = bucket_of(mh, B);
+            const uint32_t mh = window_min<NREG>(X, w, lane);
+            const uint32_t b = mh & (B - 1u);
 
             if (MODE == SM_DUMP) {
                 if (p < P.n_bases) {
@@ -237,11 +246,12 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
                 int start0 = valid && !(prev_valid && prev_b == b);
                 int rs = warp_incl_max(start0 ? lp : -1);
                 rs = rs > c_runstart ? rs : c_runstart;
-                int pos_in_run = lp - rs;
-                int q = pos_in_run / nmax;
-                int start = valid && (start0 || pos_in_run - q * nmax == 0);
-                int smstart = rs + q * nmax;
-                if (s > 0) {  // emit supermers that ended in the previous step
+                const int pos_in_run = lp - rs;
+                // pos_in_run / nmax by a multiply: exact for pos_in_run < 2^24
+                const int q = (int)__umulhi((uint32_t)pos_in_run, P.nmax_magic);
+                const int start = valid && (start0 || pos_in_run == q * nmax);
+                const int smstart = rs + q * nmax;
+                if (s > 0) {
                     int nv = __shfl_down_sync(0xffffffffu, pv, 1);
                     int ns = __shfl_down_sync(0xffffffffu, pstart, 1);
                     int v0 = __shfl_sync(0xffffffffu, valid, 0);
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
                         nv = v0;
                         ns = s0;
                     }
-                    if (pv && (!nv || ns)) emit(pb, psm, plp);
+                    emit_prev(nv, ns);
                 }
                 c_valid = __shfl_sync(0xffffffffu, valid, 31);
                 c_b = __shfl_sync(0xffffffffu, b, 31);
@@ -264,7 +274,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
             // roll the scores forward by one step
 #pragma unroll
             for (int r = 0; r + 1 < NREG; ++r) X[r] = X[r + 1];
-            X[NREG - 1] = mmer_score(wpk, 32 * (s + NREG) + lane, m, P.seed);
+            X[NREG - 1] = mmer_score(wpk, 32 * (s + NREG) + lane, m, P.seed32);
         }
         if (MODE != SM_DUMP) {  // the tile edge ends every open supermer
             int nv = __shfl_down_sync(0xffffffffu, pv, 1);
@@ -273,15 +283,16 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
                 nv = 0;
                 ns = 0;
             }
-            if (pv && (!nv || ns)) emit(pb, psm, plp);
+            emit_prev(nv, ns);
         }
         __syncwarp();
     }
 
-    if (MODE == SM_COUNT) {
+    if (MODE == SM_DESC) {
+        flush();
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-            P.cta_counts[(u64)b * P.grid + blockIdx.x] = s_cnt[b];
+            if (s_cnt[b]) atomicAdd(P.bucket_rec + b, s_cnt[b]);
             if (s_km[b]) atomicAdd(reinterpret_cast<unsigned long long*>(P.bucket_kmers + b),
                                    (unsigned long long)s_km[b]);
         }
@@ -310,25 +321,70 @@ static void launch_mode(const SmParams& p, cudaStream_t st) {
 
 void launch_supermer(int mode, const SmParams& p, cudaStream_t st) {
     if (p.n_bases == 0) return;
-    if (mode == SM_COUNT) launch_mode<SM_COUNT>(p, st);
-    else if (mode == SM_SCATTER) launch_mode<SM_SCATTER>(p, st);
+    if (mode == SM_DESC) launch_mode<SM_DESC>(p, st);
     else launch_mode<SM_DUMP>(p, st);
 }
 
 int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets) {
     size_t sm = supermer_smem_bytes(mode, n_buckets);
     int n = 0;
-    const void* fn = nullptr;
-    if (mode == SM_SCATTER) {
-        fn = wide ? (nreg == 2 ? (const void*)k_supermer<SM_SCATTER, true, 2> : (const void*)k_supermer<SM_SCATTER, true, 3>)
-                  : (nreg == 2 ? (const void*)k_supermer<SM_SCATTER, false, 2> : (const void*)k_supermer<SM_SCATTER, false, 3>);
-    } else {
-        fn = wide ? (nreg == 2 ? (const void*)k_supermer<SM_COUNT, true, 2> : (const void*)k_supermer<SM_COUNT, true, 3>)
-                  : (nreg == 2 ? (const void*)k_supermer<SM_COUNT, false, 2> : (const void*)k_supermer<SM_COUNT, false, 3>);
-    }
+    const void* fn = wide ? (nreg == 2 ? (const void*)k_supermer<SM_DESC, true, 2> : (const void*)k_supermer<SM_DESC, true, 3>)
+                          : (nreg == 2 ? (const void*)k_supermer<SM_DESC, false, 2> : (const void*)k_supermer<SM_DESC, false, 3>);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, sm) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------------------
+// records from descriptors
+// ---------------------------------------------------------------------------
+// One thread per supermer: a slot in its bucket from the bucket's cursor, the
+// record's bases gathered from the packed reads (the descriptors of a warp
+// come from one tile, so these reads hit L1/L2).
+template <bool WIDE>
+__global__ void __launch_bounds__(256) k_scatter_desc(const u64* __restrict__ desc, u64 n_desc,
+                                                      const u64* __restrict__ packed, int k,
+                                                      const u64* __restrict__ bucket_off, uint32_t* cursor,
+                                                      u64* __restrict__ records, u64 n_records, int* err) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n_desc; i += (u64)gridDim.x * blockDim.x) {
+        const u64 d = desc[i];
+        const u64 pos = d & ((1ULL << 40) - 1);
+        const uint32_t n = (uint32_t)(d >> 40) & 0xFF, b = (uint32_t)(d >> 48);
+        const u64 slot = bucket_off[b] + atomicAdd(cursor + b, 1u);
+        if (slot >= n_records || slot >= bucket_off[b + 1]) {
+            raise_error(err, HSK_DERR_BOUNDS);
+            continue;
+        }
+        const int nb = (int)n + k - 1;  // bases in the record
+        if (!WIDE) {
+            u64 a = keep_bases(extract_k64(packed, pos, 32), nb);
+            u64 c = keep_bases(extract_k64(packed, pos + 32, 32), nb - 32) | (u64)n;
+            reinterpret_cast<ulonglong2*>(records)[slot] = make_ulonglong2(a, c);
+        } else {
+            u64 r[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) r[j] = keep_bases(extract_k64(packed, pos + 32 * j, 32), nb - 32 * j);
+            r[3] |= (u64)n;
+            ulonglong2* dst = reinterpret_cast<ulonglong2*>(records) + 2 * slot;
+            dst[0] = make_ulonglong2(r[0], r[1]);
+            dst[1] = make_ulonglong2(r[2], r[3]);
+        }
+    }
+}
+
+void launch_scatter_desc(const uint64_t* desc, uint64_t n_desc, const uint64_t* packed, int k,
+                         const uint64_t* bucket_off, uint32_t* cursor, uint64_t* records, uint64_t n_records,
+                         int* err, int grid, cudaStream_t st) {
+    if (n_desc == 0) return;
+    count_launch();
+    uint64_t need = (n_desc + 255) / 256;
+    unsigned g = (unsigned)(need < (uint64_t)grid ? need : (uint64_t)grid);
+    if (k <= 32)
+        k_scatter_desc<false><<<g, 256, 0, st>>>((const u64*)desc, n_desc, (const u64*)packed, k,
+                                                 (const u64*)bucket_off, cursor, (u64*)records, n_records, err);
+    else
+        k_scatter_desc<true><<<g, 256, 0, st>>>((const u64*)desc, n_desc, (const u64*)packed, k,
+                                                (const u64*)bucket_off, cursor, (u64*)records, n_records, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -388,18 +444,6 @@ void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* st
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     count_launch();
     k_scan_u32<<<(unsigned)tiles, 256, 0, st>>>(in, n, (u64*)out, (u64*)status, tile_ctr, epoch, err);
-}
-
-__global__ void k_gather_stride(const u64* __restrict__ off, uint32_t B, uint32_t stride,
-                                u64* __restrict__ out) {
-    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b <= B) out[b] = off[(u64)b * stride];
-}
-
-void launch_gather_stride(const uint64_t* off, uint32_t B, uint32_t stride, uint64_t* out,
-                          cudaStream_t st) {
-    count_launch();
-    k_gather_stride<<<(B + 1 + 255) / 256, 256, 0, st>>>((const u64*)off, B, stride, (u64*)out);
 }
 
 }  // namespace hsk
