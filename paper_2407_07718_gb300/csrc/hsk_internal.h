@@ -95,16 +95,19 @@ void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint3
 
 // ---- S5 run-length count, filter, histogram -------------------------------
 uint64_t rle_tiles(uint64_t n, int key_words);
-uint64_t rle_status_words(uint64_t n);  // look-back words for n items
-// heads[0..D) = start index of every run; heads[D] = n; *n_heads = D.
-void launch_rle_heads(const void* keys, uint64_t n, int key_words, uint32_t* heads,
-                      uint64_t* n_heads, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch,
-                      int* err, cudaStream_t st);
-// For every run: histogram, max, filter; appends kept (key, count) at out + base.
-void launch_rle_emit(const void* keys, const uint32_t* heads, const uint64_t* n_heads,
-                     uint64_t n_heads_host, int key_words, uint32_t lo, uint32_t hi,
-                     uint64_t* hist, uint32_t hist_len, uint32_t* max_count, void* out_keys,
-                     uint32_t* out_counts, uint64_t* n_out, uint64_t* status, uint32_t* tile_ctr,
-                     uint32_t epoch, int* err, cudaStream_t st);
+uint64_t rle_bits_words(uint64_t n);
+// Pass 1: head bitmask, per-tile first/last head and kept count of the runs
+// closing inside the tile; histogram, max and head count (added into n_heads).
+void launch_rle_mark(const void* keys, uint64_t n, int key_words, uint32_t* bits, uint64_t* tile_first,
+                     uint64_t* tile_last, uint32_t* tile_keep, uint32_t lo, uint32_t hi, uint64_t* hist,
+                     uint32_t hist_len, uint32_t* max_count, uint64_t* n_heads, int grid, cudaStream_t st);
+// Pass 2: next[t] = first head after tile t (or n); closes each tile's last run.
+void launch_rle_close(const uint64_t* tile_first, const uint64_t* tile_last, uint64_t* next, uint64_t* block_min,
+                      uint64_t n_tiles, uint64_t n, uint32_t* tile_keep, uint32_t lo, uint32_t hi, uint64_t* hist,
+                      uint32_t hist_len, uint32_t* max_count, cudaStream_t st);
+// Pass 3: kept (key, count) pairs at out_off[t] (exclusive scan of tile_keep).
+void launch_rle_write(const void* keys, uint64_t n, int key_words, const uint32_t* bits, const uint64_t* next,
+                      const uint64_t* out_off, uint32_t lo, uint32_t hi, void* out_keys, uint32_t* out_counts,
+                      uint64_t out_cap, int* err, int grid, cudaStream_t st);
 
 }  // namespace hsk

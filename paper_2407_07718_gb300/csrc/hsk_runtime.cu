@@ -522,7 +522,8 @@ static int plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int ke
     return HSK_OK;
 }
 
-// Heads + emit for one sorted chunk; appends to the context's pair output.
+// Run-length count, histogram and filter of one sorted chunk; appends the
+// kept pairs to the context's output.
 int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uint32_t lo,
                   uint32_t hi, uint32_t hist_len, uint64_t* d_hist, Output& O, cudaStream_t st) {
     if (n == 0) return HSK_OK;
@@ -530,25 +531,37 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
         hsk_set_error(c, "a sort chunk of %llu keys exceeds 2^32-1", (unsigned long long)n);
         return HSK_EOVERFLOW;
     }
-    TRY(hsk_ensure(c, c->heads, (n + 1) * 4, false));
-    TRY(ensure_status(c, rle_status_words(n), st));
+    const uint64_t nt = rle_tiles(n, key_words), nb = (nt + 1023) / 1024;
+    TRY(hsk_ensure(c, c->heads, rle_bits_words(n) * 4, false));
+    TRY(hsk_ensure(c, c->rle_tiles, (nt * 8 * 4 + 8) + nt * 4 + nb * 8 + 64, false));
+    uint64_t* t_first = (uint64_t*)c->rle_tiles.p;
+    uint64_t* t_last = t_first + nt;
+    uint64_t* t_next = t_last + nt;
+    uint64_t* t_off = t_next + nt;  // nt + 1 entries
+    uint32_t* t_keep = (uint32_t*)(t_off + nt + 1);
+    uint64_t* b_min = (uint64_t*)(t_keep + ((nt + 1) & ~1ull));
+    CK(cudaMemsetAsync(c->d_nheads, 0, 8, st));
+    launch_rle_mark(sorted, n, key_words, (uint32_t*)c->heads.p, t_first, t_last, t_keep, lo, hi, d_hist,
+                    hist_len, c->d_max, c->d_nheads, c->num_sms * 4, st);
+    launch_rle_close(t_first, t_last, t_next, b_min, nt, n, t_keep, lo, hi, d_hist, hist_len, c->d_max, st);
+    TRY(ensure_status(c, scan_status_words(nt), st));
     uint32_t ep, *ctr;
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
-    launch_rle_heads(sorted, n, key_words, (uint32_t*)c->heads.p, c->d_nheads,
-                     (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    launch_scan_u32(t_keep, nt, t_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
     CK(cudaGetLastError());
-    uint64_t D = 0;
+    uint64_t D = 0, kept = 0;
     CK(cudaMemcpyAsync(&D, c->d_nheads, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&kept, t_off + nt, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     O.n_distinct += D;
-    // output capacity: previous pairs + at most D new ones (grown with copy)
-    size_t kb = (size_t)key_words * 8;
-    uint64_t need = O.n_pairs + D;
+    // output capacity: previous pairs + the kept ones (grown with copy)
+    const size_t kb = (size_t)key_words * 8;
+    const uint64_t need = O.n_pairs + kept;
     if (c->out_keys.cap < need * kb || c->out_counts.cap < need * 4) {
         DevBuf nk, ncn;
-        TRY(hsk_ensure(c, nk, need * kb, false));
-        TRY(hsk_ensure(c, ncn, need * 4, false));
+        TRY(hsk_ensure(c, nk, need * kb + need * kb / 4, false));
+        TRY(hsk_ensure(c, ncn, need * 4 + need, false));
         if (O.n_pairs) {
             CK(cudaMemcpyAsync(nk.p, c->out_keys.p, O.n_pairs * kb, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(ncn.p, c->out_counts.p, O.n_pairs * 4, cudaMemcpyDeviceToDevice, st));
@@ -559,17 +572,10 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
         c->out_keys = nk;
         c->out_counts = ncn;
     }
-    TRY(ensure_status(c, rle_status_words(D), st));
-    TRY(hsk_next_epoch(c, st, &ep));
-    TRY(hsk_next_counter(c, st, &ctr));
-    launch_rle_emit(sorted, (const uint32_t*)c->heads.p, c->d_nheads, D, key_words, lo, hi, d_hist,
-                    hist_len, c->d_max, (char*)c->out_keys.p + O.n_pairs * kb,
-                    (uint32_t*)c->out_counts.p + O.n_pairs, c->d_nout, (uint64_t*)c->lb_status.p,
-                    ctr, ep, c->d_err, st);
+    launch_rle_write(sorted, n, key_words, (const uint32_t*)c->heads.p, t_next, t_off, lo, hi,
+                     (char*)c->out_keys.p + O.n_pairs * kb, (uint32_t*)c->out_counts.p + O.n_pairs, kept,
+                     c->d_err, c->num_sms * 4, st);
     CK(cudaGetLastError());
-    uint64_t kept = 0;
-    CK(cudaMemcpyAsync(&kept, c->d_nout, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
     O.n_pairs += kept;
     return HSK_OK;
 }

@@ -96,7 +96,7 @@ struct hsk_ctx {
     DevBuf pk, iv, rs;               // S1 packed bases, invalid mask, read-start mask
     DevBuf cta_cnt, cta_off, bucket_kmers, bucket_rec, records;  // S2/S3
     DevBuf keys, alt, pass_hist, digit_off, lb_status, seg;        // S4
-    DevBuf heads, out_keys, out_counts, hist;                      // S5
+    DevBuf heads, rle_tiles, out_keys, out_counts, hist;           // S5
     DevBuf pair_alt_keys, pair_alt_counts;                         // S6
     DevBuf batch_a, batch_b, batch_c, batch_d;                     // batched form
 
@@ -117,7 +117,7 @@ struct hsk_ctx {
 
     std::vector<DevBuf*> all_bufs() {
         return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
-                &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads,
+                &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads, &rle_tiles,
                 &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &batch_a,
                 &batch_b, &batch_c, &batch_d};
     }
