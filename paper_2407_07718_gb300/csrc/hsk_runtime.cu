@@ -542,7 +542,7 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
     uint64_t* b_min = (uint64_t*)(t_keep + ((nt + 1) & ~1ull));
     CK(cudaMemsetAsync(c->d_nheads, 0, 8, st));
     launch_rle_mark(sorted, n, key_words, (uint32_t*)c->heads.p, t_first, t_last, t_keep, lo, hi, d_hist,
-                    hist_len, c->d_max, c->d_nheads, c->num_sms * 4, st);
+                    hist_len, c->d_max, c->d_nheads, c->num_sms * (key_words == 1 ? 4 : 2), st);
     launch_rle_close(t_first, t_last, t_next, b_min, nt, n, t_keep, lo, hi, d_hist, hist_len, c->d_max, st);
     TRY(ensure_status(c, scan_status_words(nt), st));
     uint32_t ep, *ctr;

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256) k_rle_mark(const K* __restrict__ keys, u6
     __shared__ uint32_t s_w[8];
     __shared__ uint32_t s_keep[8];
     __shared__ uint32_t s_fl[2];
+    __shared__ K s_edge[1 + RLE_ITEMS * 8];  // key before each run of 32 keys
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t sb = hist_len < RLE_SBINS ? hist_len : RLE_SBINS;
     for (uint32_t b = threadIdx.x; b < sb; b += 256) s_hist[b] = 0;
@@ -105,15 +106,29 @@ __global__ void __launch_bounds__(256) k_rle_mark(const K* __restrict__ keys, u6
             s_fl[0] = NO_HEAD;
             s_fl[1] = 0;
         }
-        // ---- head flags, one ballot per 32 consecutive keys
-#pragma unroll 4
+        // ---- head flags, one ballot per 32 consecutive keys; all loads first.
+        // The left neighbour of a warp's lane 0 is the last key of the previous
+        // 32, passed through shared memory (the tile's first key reads the key
+        // before the tile).
+        K cur[RLE_ITEMS];
+#pragma unroll
+        for (int i = 0; i < RLE_ITEMS; ++i) {
+            const u64 idx = base + (u64)i * 256 + warp * 32 + lane;
+            cur[i] = idx < n ? keys[idx] : K{};
+        }
+        if (threadIdx.x == 0) s_edge[0] = base > 0 ? keys[base - 1] : K{};
+        if (lane == 31) {
+#pragma unroll
+            for (int i = 0; i < RLE_ITEMS; ++i) s_edge[1 + i * 8 + warp] = cur[i];
+        }
+        __syncthreads();
+#pragma unroll
         for (int i = 0; i < RLE_ITEMS; ++i) {
             const u64 idx = base + (u64)i * 256 + warp * 32 + lane;
             const bool in = idx < n;
-            const K cur = in ? keys[idx] : K{};
-            K prv = shfl_up1(cur);
-            if (lane == 0) prv = (in && idx > 0) ? keys[idx - 1] : cur;
-            const bool head = in && (idx == 0 || !key_eq(cur, prv));
+            K prv = shfl_up1(cur[i]);
+            if (lane == 0) prv = s_edge[i * 8 + warp];  // key idx - 1
+            const bool head = in && (idx == 0 || !key_eq(cur[i], prv));
             const uint32_t word = __ballot_sync(0xffffffffu, head);
             if (lane == 0) {
                 s_bits[i * 8 + warp] = word;

@@ -70,6 +70,10 @@ __device__ __forceinline__ key128 record_kmer128(const u64 (&W)[4], uint32_t j, 
 // histogram and moves on to the next segment, so CTAs finish together.
 // Segment c: records [rec_base[c], rec_base[c+1]), keys written from
 // key_base[c]; look-back status of its tiles at status + c * st_stride.
+// A tile's records are staged in shared memory with their k-mer counts'
+// prefix; thread j of the CTA then takes keys j, j+256, ... of the tile and
+// finds each key's record by binary search, so all threads expand the same
+// number of keys and the key writes are contiguous.
 template <bool WIDE>
 __global__ void __launch_bounds__(256) k_expand_seg(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
                                                     const u64* __restrict__ key_base, uint32_t C, int k,
@@ -78,6 +82,8 @@ __global__ void __launch_bounds__(256) k_expand_seg(const u64* __restrict__ rec,
                                                     int n_pass, int* err) {
     constexpr int RW = WIDE ? 4 : 2;
     __shared__ uint32_t s_hist[MAX_PASS * RADIX];
+    extern __shared__ __align__(16) u64 s_rec[];  // EXP_TILE * RW words (dynamic)
+    __shared__ uint32_t s_pre[EXP_TILE + 1];
     __shared__ u64 s_scr[9];
     __shared__ u64 s_prefix;
     __shared__ uint32_t s_tile;
@@ -107,30 +113,32 @@ __global__ void __launch_bounds__(256) k_expand_seg(const u64* __restrict__ rec,
         }
         dirty = true;
         u64* seg_status = status + (u64)c * st_stride;
-        const u64 r0 = tile * EXP_TILE + (u64)threadIdx.x * EXP_RPT;
-        u64 W[EXP_RPT][4];
-        uint32_t nk[EXP_RPT];
-        u64 sum = 0;
+        const u64 r0 = tile * EXP_TILE;
+        const uint32_t nr = (uint32_t)(n_rec - r0 < (u64)EXP_TILE ? n_rec - r0 : (u64)EXP_TILE);
+        // ---- stage the tile's records (contiguous, 128-bit loads)
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rec + (rb + r0) * RW);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rec);
+        for (uint32_t i = threadIdx.x; i < nr * (RW / 2); i += 256) dst[i] = src[i];
+        __syncthreads();
+        // ---- k-mer counts of records 4t .. 4t+3, block scan
+        uint32_t nk[EXP_RPT], sum = 0;
 #pragma unroll
         for (int i = 0; i < EXP_RPT; ++i) {
-            nk[i] = 0;
-            W[i][0] = W[i][1] = W[i][2] = W[i][3] = 0;
-            if (r0 + i < n_rec) {
-                const u64* r = rec + (rb + r0 + i) * (u64)RW;
-                ulonglong2 a = *reinterpret_cast<const ulonglong2*>(r);
-                W[i][0] = a.x;
-                W[i][1] = a.y;
-                if (WIDE) {
-                    ulonglong2 b = *reinterpret_cast<const ulonglong2*>(r + 2);
-                    W[i][2] = b.x;
-                    W[i][3] = b.y;
-                }
-                nk[i] = (uint32_t)((WIDE ? W[i][3] : W[i][1]) & 0xFF);
-            }
+            const uint32_t r = threadIdx.x * EXP_RPT + i;
+            nk[i] = r < nr ? (uint32_t)(s_rec[r * RW + RW - 1] & 0xFF) : 0u;
             sum += nk[i];
         }
         u64 total;
-        u64 excl = block_excl_sum<256, u64>(sum, s_scr, total);
+        u64 excl = block_excl_sum<256, u64>((u64)sum, s_scr, total);
+        {
+            uint32_t run = (uint32_t)excl;
+#pragma unroll
+            for (int i = 0; i < EXP_RPT; ++i) {
+                s_pre[threadIdx.x * EXP_RPT + i] = run;
+                run += nk[i];
+            }
+            if (threadIdx.x == 255) s_pre[EXP_TILE] = run;
+        }
         if (threadIdx.x == 0) {
             u64 pre = 0;
             if (tile == 0) {
@@ -143,27 +151,34 @@ __global__ void __launch_bounds__(256) k_expand_seg(const u64* __restrict__ rec,
             s_prefix = pre;
         }
         __syncthreads();
-        u64 o = key_base[c] + s_prefix + excl;
-        if (o + sum > key_base[c + 1]) {
+        const u64 o = key_base[c] + s_prefix;
+        const uint32_t T = (uint32_t)total;
+        if (o + T > key_base[c + 1]) {
             raise_error(err, HSK_DERR_BOUNDS);
             continue;
         }
-#pragma unroll
-        for (int i = 0; i < EXP_RPT; ++i) {
-            // the record's low 8 bits of its last word hold n; they never fall
-            // inside a k-mer (n + k - 1 <= 32 * record words - 4 bases)
-            for (uint32_t j = 0; j < nk[i]; ++j, ++o) {
-                if (!WIDE) {
-                    u64 key = canonical64(record_kmer64(W[i], j, k), k);
-                    reinterpret_cast<u64*>(keys_out)[o] = key;
-                    for (int p = 0; p < n_pass; ++p)
-                        atomicAdd(&s_hist[p * RADIX + key_digit(key, 8 * p, 0xFF)], 1u);
-                } else {
-                    key128 key = canonical128(record_kmer128(W[i], j, k), k);
-                    reinterpret_cast<ulonglong2*>(keys_out)[o] = make_ulonglong2(key.lo, key.hi);
-                    for (int p = 0; p < n_pass; ++p)
-                        atomicAdd(&s_hist[p * RADIX + key_digit(key, 8 * p, 0xFF)], 1u);
-                }
+        // ---- expand: key j of the tile belongs to the last record with s_pre[r] <= j
+        for (uint32_t j = threadIdx.x; j < T; j += 256) {
+            uint32_t lo = 0, hi = nr;  // s_pre[lo] <= j < s_pre[hi]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_pre[mid] <= j) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t jj = j - s_pre[lo];
+            u64 W[4];
+            W[0] = s_rec[lo * RW];
+            W[1] = s_rec[lo * RW + 1];
+            W[2] = WIDE ? s_rec[lo * RW + 2] : 0ULL;
+            W[3] = WIDE ? s_rec[lo * RW + 3] : 0ULL;
+            if (!WIDE) {
+                u64 key = canonical64(record_kmer64(W, jj, k), k);
+                reinterpret_cast<u64*>(keys_out)[o + j] = key;
+                for (int p = 0; p < n_pass; ++p) atomicAdd(&s_hist[p * RADIX + key_digit(key, 8 * p, 0xFF)], 1u);
+            } else {
+                key128 key = canonical128(record_kmer128(W, jj, k), k);
+                reinterpret_cast<ulonglong2*>(keys_out)[o + j] = make_ulonglong2(key.lo, key.hi);
+                for (int p = 0; p < n_pass; ++p) atomicAdd(&s_hist[p * RADIX + key_digit(key, 8 * p, 0xFF)], 1u);
             }
         }
     }
@@ -179,14 +194,18 @@ void launch_expand_seg(const uint64_t* records, const uint64_t* rec_base, const 
     unsigned g = (unsigned)(want < (uint64_t)grid ? want : (uint64_t)grid);
     if (g < C) g = C;  // every segment gets a starting CTA
     const u64 stride = (max_tiles + 1) * LB_PAD;
-    if (k <= 32)
-        k_expand_seg<false><<<g, 256, 0, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)key_base, C,
+    const size_t dyn = (size_t)EXP_TILE * (k <= 32 ? 2 : 4) * sizeof(u64);
+    if (k <= 32) {
+        cudaFuncSetAttribute(k_expand_seg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        k_expand_seg<false><<<g, 256, dyn, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)key_base, C,
                                                k, keys, (u64*)status, stride, tile_ctrs, epoch, (u64*)hist,
                                                n_pass, err);
-    else
-        k_expand_seg<true><<<g, 256, 0, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)key_base, C,
-                                              k, keys, (u64*)status, stride, tile_ctrs, epoch, (u64*)hist,
-                                              n_pass, err);
+    } else {
+        cudaFuncSetAttribute(k_expand_seg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        k_expand_seg<true><<<g, 256, dyn, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)key_base, C,
+                                                k, keys, (u64*)status, stride, tile_ctrs, epoch, (u64*)hist,
+                                                n_pass, err);
+    }
 }
 
 // ---------------------------------------------------------------------------
