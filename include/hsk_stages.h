@@ -95,7 +95,7 @@ int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t
  * cudaMalloc/cudaFree can imply.  Sorts n keys of key_words words (1, or 2 as
  * {lo, hi}) in place, ascending, on the low key_bits bits (the others must be
  * zero), with the same result as hsk_stage_sort, and calls no allocating
- * routine.  Its scratch is one fixed array of about 8.7 MB that every GPU
+ * routine.  Its scratch is one fixed array of about 9.2 MB that every GPU
  * loading this library holds until the process exits; n may be at most
  * HSK_NOALLOC_MAX_KEYS_U64 (key_words = 1) or HSK_NOALLOC_MAX_KEYS_U128
  * (key_words = 2), larger n returns HSK_EOVERFLOW and does nothing.  The

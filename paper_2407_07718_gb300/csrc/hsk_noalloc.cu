@@ -25,7 +25,7 @@
 namespace {
 
 constexpr size_t ALT_BYTES = 8u << 20;                 // 2^20 x 8 B keys or 2^19 x 16 B keys
-constexpr size_t STATUS_WORDS = 256 * 256;             // 256 tiles x 256 digits
+constexpr size_t STATUS_WORDS = 512 * 256;             // 512 tiles (of >= 2048 keys) x 256 digits
 constexpr size_t HIST_WORDS = 16 * 256;                // up to 16 passes x 256 digits
 constexpr size_t OFF_ALT = 0;
 constexpr size_t OFF_STATUS = OFF_ALT + ALT_BYTES;

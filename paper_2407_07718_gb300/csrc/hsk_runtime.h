@@ -19,7 +19,9 @@
 #define HSK_N_COUNTERS 1024
 #define HSK_SMALL_BYTES 8192
 #define HSK_MAX_BUCKETS 8192
-#define HSK_SEGMENTS 64             // bucket groups sorted side by side
+#ifndef HSK_SEGMENTS
+#define HSK_SEGMENTS 256            // bucket groups sorted side by side
+#endif
 #define HSK_MIN_SEGMENT_KMERS 16384 // smaller jobs use fewer segments
 
 struct DevBuf {

@@ -263,11 +263,11 @@ void launch_digit_offsets_seg(const uint64_t* hist, const uint64_t* key_base, ui
 template <typename K>
 struct PassCfg;
 #ifndef HSK_OS_ITEMS_U64
-#define HSK_OS_ITEMS_U64 16
+#define HSK_OS_ITEMS_U64 8
 #endif
 template <>
 struct PassCfg<u64> {
-    static constexpr int ITEMS = HSK_OS_ITEMS_U64;  // 16: 4096 keys, 32 KB per tile
+    static constexpr int ITEMS = HSK_OS_ITEMS_U64;  // 8: 2048 keys, 16 KB per tile
 };
 template <>
 struct PassCfg<key128> {
@@ -421,19 +421,255 @@ static void launch_pass_t(const void* kin, void* kout, const uint32_t* vin, uint
                                                           epoch, err);
 }
 
+// ---------------------------------------------------------------------------
+// the same pass, persistent, with TMA-staged tiles (keys only)
+// ---------------------------------------------------------------------------
+// Each CTA takes tiles from the counter in order.  While it ranks, looks back
+// and scatters one tile, the keys of the next tile it has claimed are already
+// being copied into its other shared-memory buffer by a TMA bulk copy, so the
+// SM always has a tile load in flight.  A copy starts at the 16-byte boundary
+// at or below the tile (so `pre` keys of the previous tile lead the buffer)
+// and covers whole 16-byte units inside the segment; a key left over at the
+// end is loaded by one thread.  Nothing is read outside the keys.
+// Threads per CTA and keys per thread of the TMA pass (compile-time knobs);
+// CTAs per SM follow from the registers and the two staging buffers.
+#ifndef HSK_TMA_NT
+#define HSK_TMA_NT 256
+#endif
+#ifndef HSK_TMA_CTAS
+#define HSK_TMA_CTAS 4
+#endif
+template <typename K>
+struct TmaCfg;
+template <>
+struct TmaCfg<u64> {
+    static constexpr int NT = HSK_TMA_NT, ITEMS = 256 * HSK_OS_ITEMS_U64 / HSK_TMA_NT;
+};
+template <>
+struct TmaCfg<key128> {
+    static constexpr int NT = HSK_TMA_NT, ITEMS = 256 * 8 / HSK_TMA_NT;
+};
+template <typename K>
+constexpr int tma_buf_bytes() {
+    return ((TmaCfg<K>::NT * TmaCfg<K>::ITEMS * (int)sizeof(K) + 16) + 127) & ~127;
+}
+// the host sizes segments' tile counts with the PassCfg tile: keep them equal
+static_assert(TmaCfg<u64>::NT * TmaCfg<u64>::ITEMS == 256 * PassCfg<u64>::ITEMS, "tile sizes differ");
+static_assert(TmaCfg<key128>::NT * TmaCfg<key128>::ITEMS == 256 * PassCfg<key128>::ITEMS, "tile sizes differ");
+
+template <typename K>
+__global__ void __launch_bounds__(TmaCfg<K>::NT, HSK_TMA_CTAS)
+    k_onesweep_tma(const K* __restrict__ kin, K* __restrict__ kout, const u64* __restrict__ key_base, uint32_t C,
+                   uint32_t tmax, int shift, const u64* __restrict__ doff, u64* status, uint32_t* tile_ctr,
+                   uint32_t epoch, int* err) {
+    constexpr int NT = TmaCfg<K>::NT;
+    constexpr int ITEMS = TmaCfg<K>::ITEMS;
+    constexpr int TILE = NT * ITEMS;
+    constexpr int WARPS = NT / 32;
+    constexpr int BUF = tma_buf_bytes<K>();
+    extern __shared__ __align__(128) unsigned char smem_tma[];  // two staging buffers of BUF bytes
+    __shared__ uint32_t s_whist[WARPS][RADIX];
+    __shared__ uint32_t s_tstart[RADIX];
+    __shared__ u64 s_gbase[RADIX];
+    __shared__ uint32_t s_scr[NT / 32 + 1];
+    __shared__ __align__(8) u64 s_bar[2];
+    __shared__ uint32_t s_next;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t total = C * tmax;
+
+    // geometry of global tile g: segment g % C, tile g / C of that segment
+    auto geom = [&](uint32_t g, u64& sb, u64& seg_end, u64& base, uint32_t& n_t) -> bool {
+        const uint32_t c = g % C, j = g / C;
+        sb = key_base[c];
+        seg_end = key_base[c + 1];
+        base = sb + (u64)j * TILE;
+        if (base >= seg_end) return false;
+        n_t = (uint32_t)(seg_end - base < (u64)TILE ? seg_end - base : (u64)TILE);
+        return true;
+    };
+    auto lead = [&](u64 base) -> uint32_t {
+        return (uint32_t)((reinterpret_cast<uintptr_t>(kin + base) & 15) / sizeof(K));
+    };
+    // thread 0: start the copy of tile g into buffer b (returns whether one started)
+    int outstanding[2] = {0, 0};  // thread 0: a copy into buffer b not yet waited for
+    auto issue = [&](uint32_t g, int b) -> bool {
+        u64 sb, se, base;
+        uint32_t n_t;
+        if (!geom(g, sb, se, base, n_t)) return false;
+        outstanding[b] = 1;
+        const uint32_t pre = lead(base);
+        const uint32_t bulk = ((n_t + pre) * (uint32_t)sizeof(K)) & ~15u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar[b], bulk);
+        if (bulk)
+            tma_load_1d(smem_tma + b * BUF, reinterpret_cast<const unsigned char*>(kin + base) - pre * sizeof(K), bulk,
+                        &s_bar[b]);
+        return true;
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_init_fence();
+        const uint32_t g0 = atomicAdd(tile_ctr, 1u);
+        s_next = g0;
+        if (g0 < total) issue(g0, 0);
+    }
+    __syncthreads();
+    uint32_t g = s_next;
+    uint32_t ph0 = 0, ph1 = 0;
+    int b = 0;
+    bool failed = false;
+    while (g < total) {
+        __syncthreads();  // s_next consumed; buffer b ^ 1 idle since the last iteration
+        if (threadIdx.x == 0) {
+            const uint32_t gn = atomicAdd(tile_ctr, 1u);
+            s_next = gn;
+            if (gn < total) issue(gn, b ^ 1);
+        }
+        for (int i = threadIdx.x; i < WARPS * RADIX; i += NT) (&s_whist[0][0])[i] = 0;
+        u64 sb, seg_end, base;
+        uint32_t tile_n;
+        if (geom(g, sb, seg_end, base, tile_n)) {
+            const uint32_t parity = b ? ph1 : ph0;
+            if (mbar_wait(&s_bar[b], parity, err)) {  // phase done: the next use waits on the other parity
+                if (b) ph1 ^= 1u;
+                else ph0 ^= 1u;
+                outstanding[b] = 0;
+            } else {
+                failed = true;
+            }
+            K* stage = reinterpret_cast<K*>(smem_tma + b * BUF);
+            const uint32_t pre = lead(base);
+            const uint32_t bulk_keys = (((tile_n + pre) * (uint32_t)sizeof(K)) & ~15u) / (uint32_t)sizeof(K);
+            if (threadIdx.x == 0 && bulk_keys < tile_n + pre) stage[tile_n + pre - 1] = kin[base + tile_n - 1];
+            __syncthreads();
+            if (__syncthreads_or(failed)) break;  // a copy never arrived: stop (the error word is set)
+
+            const int wvalid = (int)tile_n - warp * (ITEMS * 32) > 0
+                                   ? ((int)tile_n - warp * (ITEMS * 32) < ITEMS * 32 ? (int)tile_n - warp * (ITEMS * 32)
+                                                                                      : ITEMS * 32)
+                                   : 0;
+            const K* wk = stage + pre + warp * (ITEMS * 32);
+            K key[ITEMS];
+            uint32_t rank2[ITEMS / 2];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) key[i] = i * 32 + lane < wvalid ? wk[i * 32 + lane] : K{};
+            // ---- rank within the warp, in index order (stable)
+            const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const bool ok = i * 32 + lane < wvalid;
+                uint32_t d = ok ? key_digit(key[i], shift, 0xFF) : RADIX;
+                uint32_t peers = __match_any_sync(0xffffffffu, d);
+                uint32_t below = __popc(peers & lt);
+                uint32_t cnt = __popc(peers);
+                uint32_t bb = ok ? s_whist[warp][d] : 0u;
+                __syncwarp();
+                if (ok && below == 0) s_whist[warp][d] = bb + cnt;
+                __syncwarp();
+                uint32_t r = bb + below;
+                if (i & 1) rank2[i / 2] |= r << 16;
+                else rank2[i / 2] = r;
+            }
+            __syncthreads();  // every key is in registers: the buffer may be overwritten
+            const uint32_t d = threadIdx.x;  // threads 0..255: one digit each
+            const bool dig = d < RADIX;
+            uint32_t cnt = 0;
+            if (dig) {
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) {
+                    uint32_t cc = s_whist[w][d];
+                    s_whist[w][d] = cnt;
+                    cnt += cc;
+                }
+            }
+            const uint32_t c = g % C, tile = g / C;
+            u64* seg_status = status + (u64)c * tmax * RADIX;
+            u64* my = seg_status + (u64)tile * RADIX + d;
+            if (dig) {
+                if (tile == 0) st_relaxed(my, lb_word(LB_PREFIX, epoch, cnt));
+                else st_relaxed(my, lb_word(LB_AGG, epoch, cnt));
+            }
+            uint32_t tot;
+            const uint32_t tstart = block_excl_sum<NT, uint32_t>(cnt, s_scr, tot);
+            if (dig) s_tstart[d] = tstart;
+            __syncthreads();
+            // ---- place keys in the buffer in tile-sorted order (from index 0)
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                if (i * 32 + lane < wvalid) {
+                    uint32_t dd = key_digit(key[i], shift, 0xFF);
+                    uint32_t rr = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
+                    stage[s_tstart[dd] + s_whist[warp][dd] + rr] = key[i];
+                }
+            }
+            // ---- look back for the tile's offset of digit d within its segment
+            if (dig) {
+                u64 excl = 0;
+                if (tile > 0) {
+                    excl = lookback_exclusive_win<8>(seg_status + d, RADIX, tile, epoch, err);
+                    st_relaxed(my, lb_word(LB_PREFIX, epoch, excl + cnt));
+                }
+                s_gbase[d] = doff[(u64)c * RADIX + d] + excl - tstart;
+            }
+            __syncthreads();
+            // ---- scatter: consecutive threads write consecutive slots of a digit
+            for (uint32_t j = threadIdx.x; j < tile_n; j += NT) {
+                K kk = stage[j];
+                u64 pos = s_gbase[key_digit(kk, shift, 0xFF)] + j;
+                if (pos < sb || pos >= seg_end) {
+                    raise_error(err, HSK_DERR_BOUNDS);
+                    continue;
+                }
+                kout[pos] = kk;
+            }
+        }
+        __syncthreads();  // buffer b free again; s_next visible
+        g = s_next;
+        b ^= 1;
+    }
+    if (failed && threadIdx.x == 0) {
+        // a copy did not arrive in time: give the copies still in flight a
+        // bounded chance to land before the CTA's shared memory is released
+        if (outstanding[0]) mbar_wait(&s_bar[0], ph0, nullptr);
+        if (outstanding[1]) mbar_wait(&s_bar[1], ph1, nullptr);
+    }
+}
+
 void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
                          const uint64_t* key_base, uint32_t C, uint32_t tmax, int key_words, int shift,
                          const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err,
                          cudaStream_t st) {
     if (C == 0 || tmax == 0) return;
     bool hv = vin != nullptr;
-    if (key_words == 1) {
-        if (hv) launch_pass_t<u64, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
-        else launch_pass_t<u64, false>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
-    } else {
-        if (hv) launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
-        else launch_pass_t<key128, false>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
+    if (!hv) {  // persistent, TMA-staged pass
+        static int num_sms = 0;
+        if (!num_sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+            if (num_sms <= 0) num_sms = 1;
+        }
+        const uint64_t tiles = (uint64_t)C * tmax;
+        const unsigned grid = (unsigned)(tiles < (uint64_t)num_sms * HSK_TMA_CTAS ? tiles : (uint64_t)num_sms * HSK_TMA_CTAS);
+        count_launch();
+        if (key_words == 1) {
+            const size_t smem = 2 * (size_t)tma_buf_bytes<u64>();
+            cudaFuncSetAttribute(k_onesweep_tma<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_onesweep_tma<u64><<<grid, TmaCfg<u64>::NT, smem, st>>>((const u64*)kin, (u64*)kout, (const u64*)key_base, C, tmax,
+                                                         shift, (const u64*)doff, (u64*)status, tile_ctr, epoch, err);
+        } else {
+            const size_t smem = 2 * (size_t)tma_buf_bytes<key128>();
+            cudaFuncSetAttribute(k_onesweep_tma<key128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_onesweep_tma<key128><<<grid, TmaCfg<key128>::NT, smem, st>>>((const key128*)kin, (key128*)kout, (const u64*)key_base,
+                                                            C, tmax, shift, (const u64*)doff, (u64*)status, tile_ctr,
+                                                            epoch, err);
+        }
+        return;
     }
+    if (key_words == 1) launch_pass_t<u64, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
+    else launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
 }
 
 }  // namespace hsk
