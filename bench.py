@@ -13,7 +13,11 @@ steps.
 Printed JSON line: value = k-mers counted / s over all ranks; e2e = the same
 through hsk_count() with pinned host buffers (copies inside the timed region);
 roofline = the dominant kernel (the onesweep radix pass) against the measured
-HBM copy bandwidth; cpu_baseline = the CPU oracle on a bounded sample.
+HBM copy bandwidth; cpu_baseline = the CPU oracle on a bounded sample.  On one
+GPU the line also carries "batched" (256 independent read sets through
+hsk_count_batch against the same sets run one by one through hsk_count) and
+"served" (a Poisson request stream through hsk_submit/hsk_wait: throughput
+and p50/p99/p99.9 latency, against the plain per-job path).
 
 --impl reference times the CPU oracle (single thread) on a bounded sample of
 the same workload.  Under torchrun every rank runs an independent replica
@@ -150,6 +154,141 @@ def run_cpu_oracle(rs, target_windows: int, steps: int = 1):
     return nw, times, n
 
 
+# ---------------------------------------------------------------------------
+# batched and served forms against the plain per-job path
+# ---------------------------------------------------------------------------
+
+def _pinned(rs):
+    """The read set's arrays copied into page-locked host memory."""
+    import torch
+    r = torch.empty(rs.n_bases, dtype=torch.uint8, pin_memory=True)
+    r.numpy()[:] = rs.reads
+    o = torch.empty(rs.offsets.size, dtype=torch.int64, pin_memory=True)
+    o.numpy()[:] = rs.offsets.view(np.int64)
+    return (r.numpy(), o.numpy().view(np.uint64), rs.k, rs.m, rs.lo, rs.hi)
+
+
+def _generate(fn, params):
+    """Simulate the read sets on all host cores (the simulator releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(32, os.cpu_count() or 1))) as ex:
+        return list(ex.map(lambda p: _pinned(fn(*p)), params))
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def _fifo_latency(arrivals, service):
+    """Latency of each job on one first-come-first-served server."""
+    t, lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        t = max(t, a) + s
+        lat.append(t - a)
+    return lat
+
+
+def _plain_pass(ctx, jobs):
+    """Run the jobs one after another through hsk_count; per-job seconds."""
+    times, res = [], []
+    for j in jobs:
+        t0 = time.perf_counter()
+        r = ctx.count(*j, copy=False)
+        times.append(time.perf_counter() - t0)
+        res.append(r)
+    return times, res
+
+
+def bench_batched(hsk, device: int, n_sets: int, scale: float) -> dict:
+    import datagen
+    params = datagen.batched_set_params(n_sets=n_sets, scale=scale)
+    t0 = time.perf_counter()
+    jobs = _generate(datagen.batched_set, params)
+    gen_s = time.perf_counter() - t0
+    bases = sum(int(j[0].size) for j in jobs)
+    with hsk.Context(device=device) as ctx:
+        big = max(range(len(jobs)), key=lambda i: jobs[i][0].size)
+        ctx.count(*jobs[big], copy=False)          # warm: the arena grows to the largest set
+        plain_t, plain_r = _plain_pass(ctx, jobs)
+        ctx.count_batch(jobs, copy=False)           # warm: every slot grows its arena
+        t0 = time.perf_counter()
+        batch_r = ctx.count_batch(jobs, copy=False)
+        batch_s = time.perf_counter() - t0
+    for a, b in zip(plain_r, batch_r):
+        assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct, b.extra["n_pairs"])
+    n = sum(r.n_windows for r in plain_r)
+    plain_s = sum(plain_t)
+    return {"workload": f"{n_sets} sets, genome log-uniform [0.1, 20] Mbp x {scale:g}, coverage U[10, 40]x, "
+                        "150 bp reads, 1% sub, k=31 m=17, filter [2,1000]",
+            "n_sets": n_sets, "n_bases": bases, "n_windows": n, "generate_s": gen_s,
+            "plain": {"value": n / plain_s, "makespan_s": plain_s,
+                      "job_p50_ms": _pct(plain_t, 50) * 1e3, "job_p99_ms": _pct(plain_t, 99) * 1e3},
+            "batched": {"value": n / batch_s, "makespan_s": batch_s},
+            "speedup": plain_s / batch_s, "unit": UNIT,
+            "note": "makespans include host-to-device copies from pinned memory and result copies back"}
+
+
+def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget: int) -> dict:
+    import datagen
+    params = datagen.served_request_params(n=n_req, scale=scale)
+    t0 = time.perf_counter()
+    jobs = _generate(datagen.served_request, params)
+    gen_s = time.perf_counter() - t0
+    with hsk.Context(device=device, hbm_budget=budget) as ctx:
+        for kk in sorted({j[2] for j in jobs}):     # warm each key width on the largest request
+            big = max((i for i in range(len(jobs)) if jobs[i][2] == kk), key=lambda i: jobs[i][0].size)
+            ctx.count(*jobs[big], copy=False)
+        plain_t, plain_r = _plain_pass(ctx, jobs)
+        n = sum(r.n_windows for r in plain_r)
+
+        def closed_batch():
+            t0 = time.perf_counter()
+            ts = [ctx.submit(*j) for j in jobs]
+            for t in ts:
+                ctx.wait(t, copy=False)
+            dt = time.perf_counter() - t0
+            for t in ts:
+                ctx.release(t)
+            return dt
+
+        closed_batch()                              # warm the slots
+        sat_s = closed_batch()
+        rate = load * len(jobs) / sat_s             # requests per second offered
+        gaps = np.random.default_rng(5).exponential(1.0 / rate, len(jobs))
+        arrivals = np.cumsum(gaps) - gaps[0]
+        tickets = []
+        t0 = time.perf_counter()
+        for i, j in enumerate(jobs):
+            while True:
+                d = arrivals[i] - (time.perf_counter() - t0)
+                if d <= 0:
+                    break
+                time.sleep(min(d, 0.002))
+            tickets.append(ctx.submit(*j))
+        res = [ctx.wait(t, copy=False) for t in tickets]
+        open_s = time.perf_counter() - t0
+        lat = [sum(ctx.times(t)) for t in tickets]
+        for t in tickets:
+            ctx.release(t)
+    for a, b in zip(plain_r, res):
+        assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct, b.extra["n_pairs"])
+    plain_s = sum(plain_t)
+    plain_lat = _fifo_latency(arrivals, plain_t)
+    return {"workload": f"{n_req} Poisson requests, genome log-normal (median 2 Mbp, sigma_ln 1, [0.05, 50] Mbp) "
+                        f"x {scale:g}, coverage U[10, 30]x, 150 bp or 10 kb reads, k in {{21, 31, 55}}, filter [2,1000]",
+            "n_requests": n_req, "n_windows": n, "generate_s": gen_s, "hbm_budget": budget,
+            "offered_rate_per_s": rate, "load": load,
+            "served": {"value_saturated": n / sat_s, "makespan_saturated_s": sat_s,
+                       "value": n / open_s, "p50_ms": _pct(lat, 50) * 1e3, "p99_ms": _pct(lat, 99) * 1e3,
+                       "p999_ms": _pct(lat, 99.9) * 1e3},
+            "plain": {"value": n / plain_s, "makespan_s": plain_s,
+                      "p50_ms": _pct(plain_lat, 50) * 1e3, "p99_ms": _pct(plain_lat, 99) * 1e3,
+                      "p999_ms": _pct(plain_lat, 99.9) * 1e3,
+                      "latency_model": "measured per-job times on one FIFO server at the same arrival times"},
+            "speedup_saturated": plain_s / sat_s, "unit": UNIT,
+            "note": "latency = submit to completion; copies from pinned host memory inside every job"}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,6 +332,13 @@ def main():
     ap.add_argument("--cpu-windows", type=int, default=20_000_000,
                     help="windows in the oracle's bounded sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--batched-sets", type=int, default=256)
+    ap.add_argument("--batched-scale", type=float, default=1.0)
+    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-scale", type=float, default=1.0)
+    ap.add_argument("--served-load", type=float, default=0.7)
+    ap.add_argument("--served-budget", type=float, default=120e9)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -257,33 +403,50 @@ def main():
     launches = hsk.Context.launch_count() - launches0
     ms = e0.elapsed_time(e1)
     stage_ms, passes = ctx.profile_read(reset=True)
+    overflow = ctx.last_overflow()
     ctx.profile(False)
     ms_max = reduce_max(pg, ms, dev)
     total_windows = reduce_sum(pg, float(n_windows) * args.steps, dev)
     value = total_windows / (ms_max / 1e3)
 
-    # roofline of the dominant kernel: the onesweep LSD pass
+    # roofline of the dominant kernel
     peaks = measured_peaks()
     kb = 8 * kw
-    pass_ms = stage_ms[4] / max(passes, 1)
-    bytes_per_pass = n_windows * 2 * kb  # read + write every key once
-    achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9 if pass_ms > 0 else 0.0
-    sha = source_sha(os.path.join(ROOT, "paper_2407_07718_gb300", "csrc", "k_sort.cu"))
+    if passes > 0:  # global radix passes: one onesweep LSD pass reads and writes every key
+        kernel = "k_onesweep_tma (8-bit LSD pass)"
+        src = "k_sort.cu"
+        launch_ms = stage_ms[4] / passes
+        bytes_per_launch = n_windows * 2 * kb
+    else:           # on-chip path: the sub-segment sort reads every key once, writes the kept pairs
+        kernel = "k_local_sort (sub-segment sort + count in shared memory)"
+        src = "k_local.cu"
+        launch_ms = stage_ms[4] / args.steps
+        bytes_per_launch = n_windows * kb + int(res.n_pairs) * (kb + 4)
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+    sha = source_sha(os.path.join(ROOT, "paper_2407_07718_gb300", "csrc", src))
     traffic = NCU_TRAFFIC.get((args.workload, sha))
     # end-to-end algorithmic bytes per window (byte model of the whole path)
     n_sm = int(res.n_supermers)
     rec_b = 16 if kw == 1 else 32
     P = (2 * rs.k + 7) // 8
+    if passes > 0:
+        s45 = (n_sm * rec_b                                # S4: records read
+               + n_windows * kb * (1 + 2 * P)              # keys written, P passes
+               + n_windows * kb + int(res.n_pairs) * (kb + 4))  # S5: keys read, kept pairs written
+    else:
+        s45 = (2 * n_sm * rec_b                            # S4: records read to count, then to scatter
+               + n_windows * kb * 2                        # keys written by the scatter, read on chip
+               + int(res.n_pairs) * (kb + 4) * 3)          # kept pairs written, compacted (read + write)
     e2e_bytes = (rs.n_bases * (1 + 0.25 + 0.25)            # S1: ASCII in, packed + masks out
                  + 2 * rs.n_bases * 0.5                    # S2 + S3: packed + masks read twice
-                 + n_sm * rec_b * 2                        # S3 records written, S4 read
-                 + n_windows * kb * (1 + 2 * P)            # S4: keys written, P passes
-                 + n_windows * kb + int(res.n_distinct) * (4 + 4) + int(res.n_pairs) * (kb + 4))  # S5
+                 + n_sm * rec_b                            # S3 records written
+                 + s45
+                 + int(res.n_pairs) * (kb + 4) * 2 * P)    # S6: output pairs sorted
     step_s = ms_max / args.steps / 1e3
-    roofline = {"bound": "hbm", "kernel": "k_onesweep (8-bit LSD pass)", "achieved": achieved,
+    roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "traffic": traffic, "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs copy bandwidth)",
-                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms, "passes_per_step": passes / args.steps,
+                "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms, "passes_per_step": passes / args.steps,
                 "end_to_end": {"bytes_per_step": e2e_bytes, "achieved": e2e_bytes / step_s / 1e9,
                                "frac": e2e_bytes / step_s / 1e9 / peaks["hbm_gbs"]}}
 
@@ -310,6 +473,15 @@ def main():
         cpu = {"value": nw / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {nreads} reads of the workload ({nw} windows), single-thread C++ std::sort oracle, {times[0]:.1f} s"}
 
+    ctx.close()
+    del d_reads, d_offs
+    forms = {}
+    if rank == 0 and world == 1 and not args.no_forms:
+        torch.cuda.empty_cache()
+        forms["batched"] = bench_batched(hsk, local, args.batched_sets, args.batched_scale)
+        forms["served"] = bench_served(hsk, local, args.served_requests, args.served_scale, args.served_load,
+                                       int(args.served_budget))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -317,12 +489,13 @@ def main():
                 "data": "synthetic", "config": dict(config, n_windows=n_windows,
                                                      n_distinct=int(res.n_distinct), n_pairs=int(res.n_pairs),
                                                      n_supermers=n_sm, n_chunks=int(res.n_chunks),
+                                                     keys_off_chip=overflow,
                                                      parallelism=f"replicas x{world}"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "stages_ms_per_step": {n: v / args.steps for n, v in zip(hsk.Context.STAGES, stage_ms)}}
+        line.update(forms)
         print(json.dumps(line))
-    ctx.close()
     if pg is not None:
         pg.destroy_process_group()
 

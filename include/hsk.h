@@ -60,6 +60,10 @@ typedef struct {
     uint32_t max_chunk_kmers; /* 0 = as many as the budget allows; else cap per sort chunk */
     uint64_t seed;         /* XOR-ed into each canonical m-mer before hashing */
     int autotune;          /* 1 = pick bucket count and chunking per job */
+    int local_sort;        /* 1 (default) = sort and count sub-segments that fit in
+                              shared memory on chip, the rest with global radix
+                              passes; 0 = global radix passes only.  The result is
+                              the same either way. */
 } hsk_config;
 
 /* A counting result.  All arrays are owned by the context and stay valid until

@@ -109,12 +109,15 @@ int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t
 #define HSK_NOALLOC_MAX_KEYS_U128 (1u << 19)
 int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words, int key_bits, void* stream);
 
-/* Test hooks.  hsk_debug_fail_alloc_after(ctx, n): the n-th following device
+/* Test and diagnostic hooks.  hsk_debug_fail_alloc_after(ctx, n): the n-th following device
  * allocation of the context fails as if the budget were exhausted (-1 turns
  * this off), to check that every caller returns HSK_ENOMEM cleanly.
  * hsk_debug_allocated: bytes of device memory the context holds now. */
 int hsk_debug_fail_alloc_after(hsk_ctx* ctx, int n);
 uint64_t hsk_debug_allocated(hsk_ctx* ctx);
+/* Keys of the context's last counting call that did not fit the on-chip
+ * sort and went through the global radix passes instead (0 when none). */
+uint64_t hsk_debug_last_overflow(hsk_ctx* ctx);
 
 /* Profiling hooks.  When enabled, each counting call on the context records
  * CUDA events on its own stream at the boundaries of its stages and adds the

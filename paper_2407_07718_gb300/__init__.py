@@ -40,7 +40,8 @@ class HskError(RuntimeError):
 class _Config(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_uint64), ("hist_len", C.c_uint32),
                 ("n_buckets", C.c_uint32), ("radix_bits", C.c_uint32),
-                ("max_chunk_kmers", C.c_uint32), ("seed", C.c_uint64), ("autotune", C.c_int)]
+                ("max_chunk_kmers", C.c_uint32), ("seed", C.c_uint64), ("autotune", C.c_int),
+                ("local_sort", C.c_int)]
 
 
 class _Result(C.Structure):
@@ -92,6 +93,7 @@ def load():
             "hsk_stage_order": ([P, P, P, u64, i32, i32, P], i32),
             "hsk_debug_fail_alloc_after": ([P, i32], i32),
             "hsk_debug_allocated": ([P], u64),
+            "hsk_debug_last_overflow": ([P], u64),
             "hsk_profile_enable": ([P, i32], i32),
             "hsk_profile_read": ([P, C.POINTER(d), C.POINTER(u64), i32], i32),
             "hsk_launch_count": ([], u64),
@@ -155,7 +157,16 @@ class CountResult:
     extra: dict = field(default_factory=dict)
 
 
-def _host_result(r: _Result) -> CountResult:
+def _summary(r: _Result) -> CountResult:
+    """Scalars of a result only (its arrays stay in library memory, unread)."""
+    return CountResult(None, None, None, int(r.n_windows), int(r.n_distinct), int(r.max_count),
+                       int(r.key_words), int(r.n_chunks), int(r.n_supermers), float(r.device_ms),
+                       extra={"n_pairs": int(r.n_pairs)})
+
+
+def _host_result(r: _Result, copy: bool = True) -> CountResult:
+    if not copy:
+        return _summary(r)
     n, kw = int(r.n_pairs), int(r.key_words)
     if n:
         kmers = np.ctypeslib.as_array(C.cast(r.kmers, C.POINTER(C.c_uint64)), shape=(n * kw,)).copy()
@@ -174,12 +185,14 @@ class Context:
     """One library context (device arena, stream, serving slots) on one GPU."""
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, hist_len: int = 65536, n_buckets: int = 0,
-                 max_chunk_kmers: int = 0, seed: int = DEFAULT_SEED, autotune: bool = True):
+                 max_chunk_kmers: int = 0, seed: int = DEFAULT_SEED, autotune: bool = True,
+                 local_sort: bool = True):
         self.lib = load()
         cfg = _Config()
         self.lib.hsk_config_default(C.byref(cfg))
         cfg.device, cfg.hbm_budget, cfg.hist_len = device, hbm_budget, hist_len
         cfg.n_buckets, cfg.max_chunk_kmers, cfg.seed, cfg.autotune = n_buckets, max_chunk_kmers, seed, int(autotune)
+        cfg.local_sort = int(local_sort)
         h = C.c_void_p()
         rc = self.lib.hsk_create(C.byref(h), C.byref(cfg))
         if rc != HSK_OK:
@@ -209,13 +222,15 @@ class Context:
             raise HskError(rc, self.lib.hsk_last_error(self.h).decode())
 
     # ---- plain path -----------------------------------------------------------
-    def count(self, reads, offsets, k: int, m: int, lo: int, hi: int) -> CountResult:
-        """Host arrays in, host arrays out (copies inside the call)."""
+    def count(self, reads, offsets, k: int, m: int, lo: int, hi: int, copy: bool = True) -> CountResult:
+        """Host arrays in, host arrays out (copies inside the call).  With
+        copy=False only the scalars are returned; the arrays stay in the
+        context's host memory until its next call."""
         reads, offsets = _u8(reads), _u64(offsets)
         r = _Result()
         self._check(self.lib.hsk_count(self.h, _ptr(reads), _ptr(offsets), offsets.size - 1, k, m,
                                        lo, hi, C.byref(r)))
-        return _host_result(r)
+        return _host_result(r, copy)
 
     def count_device(self, reads_t, offsets_t, k: int, m: int, lo: int, hi: int, stream=None,
                      n_bases: int | None = None) -> _Result:
@@ -242,8 +257,8 @@ class Context:
                            int(r.n_chunks), int(r.n_supermers), float(r.device_ms))
 
     # ---- batched form ---------------------------------------------------------
-    def count_batch(self, jobs) -> list[CountResult]:
-        """jobs: iterable of (reads, offsets, k, m, lo, hi) host arrays."""
+    def count_batch(self, jobs, copy: bool = True) -> list[CountResult]:
+        """jobs: sequence of (reads, offsets, k, m, lo, hi) host arrays."""
         keep, arr = [], (_Job * max(len(jobs), 1))()
         for i, (reads, offsets, k, m, lo, hi) in enumerate(jobs):
             reads, offsets = _u8(reads), _u64(offsets)
@@ -252,7 +267,7 @@ class Context:
                           offsets.size - 1, k, m, lo, hi)
         outs = (_Result * max(len(jobs), 1))()
         self._check(self.lib.hsk_count_batch(self.h, arr, len(jobs), outs))
-        return [_host_result(outs[i]) for i in range(len(jobs))]
+        return [_host_result(outs[i], copy) for i in range(len(jobs))]
 
     # ---- served form ----------------------------------------------------------
     def submit(self, reads, offsets, k: int, m: int, lo: int, hi: int) -> int:
@@ -269,10 +284,10 @@ class Context:
         self._check(self.lib.hsk_poll(self.h, ticket, C.byref(d)))
         return bool(d.value)
 
-    def wait(self, ticket: int) -> CountResult:
+    def wait(self, ticket: int, copy: bool = True) -> CountResult:
         r = _Result()
         self._check(self.lib.hsk_wait(self.h, ticket, C.byref(r)))
-        return _host_result(r)
+        return _host_result(r, copy)
 
     def times(self, ticket: int) -> tuple[float, float]:
         q, x = C.c_double(), C.c_double()
@@ -350,3 +365,8 @@ class Context:
 
     def allocated(self) -> int:
         return int(self.lib.hsk_debug_allocated(self.h))
+
+    def last_overflow(self) -> int:
+        """Keys of the last call that went through the global radix passes
+        because their sub-segment did not fit the on-chip sort."""
+        return int(self.lib.hsk_debug_last_overflow(self.h))

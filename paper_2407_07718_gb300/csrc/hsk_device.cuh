@@ -7,6 +7,8 @@
 // and the canonical form are this library's reading of it).
 #pragma once
 
+#include <type_traits>
+
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -313,6 +315,63 @@ __device__ __forceinline__ T block_excl_sum(T v, T* scratch, T& total) {
     total = scratch[NT / 32];
     __syncthreads();
     return r;
+}
+
+
+// ---------------------------------------------------------------------------
+// supermer records -> k-mers
+// ---------------------------------------------------------------------------
+constexpr int EXP_RPT = 4;                 // records per thread
+constexpr int EXP_TILE = 256 * EXP_RPT;    // records per tile of the expanding kernels
+
+__device__ __forceinline__ u64 sel4(const u64 (&W)[4], uint32_t i) {
+    return i == 0 ? W[0] : i == 1 ? W[1] : i == 2 ? W[2] : i == 3 ? W[3] : 0ULL;
+}
+
+// k-mer j (k <= 32) of a record held in registers (no local-memory indexing).
+__device__ __forceinline__ u64 record_kmer64(const u64 (&W)[4], uint32_t j, int k) {
+    uint32_t i = j >> 5, off = (j & 31) * 2;
+    return funnel64(sel4(W, i), sel4(W, i + 1), off) >> (64 - 2 * k);
+}
+
+// k-mer j (33 <= k <= 64) of a record held in registers.
+__device__ __forceinline__ key128 record_kmer128(const u64 (&W)[4], uint32_t j, int k) {
+    uint32_t i = j >> 5, off = (j & 31) * 2;
+    u64 a = funnel64(sel4(W, i), sel4(W, i + 1), off);
+    u64 b = funnel64(sel4(W, i + 1), sel4(W, i + 2), off);
+    int s = 128 - 2 * k;
+    key128 r;
+    if (s == 0) {
+        r.hi = a;
+        r.lo = b;
+    } else {
+        r.hi = a >> s;
+        r.lo = (b >> s) | (a << (64 - s));
+    }
+    return r;
+}
+
+// Key j of a tile of nr records staged in shared memory (s_rec, record_words
+// words each) whose k-mer counts have the exclusive prefix s_pre[0..nr]: the
+// key belongs to the last record r with s_pre[r] <= j.
+template <bool WIDE>
+__device__ __forceinline__ typename std::conditional<WIDE, key128, u64>::type
+tile_key(const u64* s_rec, const uint32_t* s_pre, uint32_t nr, uint32_t j, int k) {
+    constexpr int RW = WIDE ? 4 : 2;
+    uint32_t lo = 0, hi = nr;  // s_pre[lo] <= j < s_pre[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_pre[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t jj = j - s_pre[lo];
+    u64 W[4];
+    W[0] = s_rec[lo * RW];
+    W[1] = s_rec[lo * RW + 1];
+    W[2] = WIDE ? s_rec[lo * RW + 2] : 0ULL;
+    W[3] = WIDE ? s_rec[lo * RW + 3] : 0ULL;
+    if constexpr (WIDE) return canonical128(record_kmer128(W, jj, k), k);
+    else return canonical64(record_kmer64(W, jj, k), k);
 }
 
 }  // namespace hsk

@@ -94,6 +94,26 @@ void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint3
                          cudaStream_t st);
 
 // ---- S5 run-length count, filter, histogram -------------------------------
+// on-chip sort of sub-segments (k_local.cu)
+size_t part_smem_bytes(int mode, int k);
+void launch_part(int mode, const uint64_t* records, const uint64_t* rec_base, const uint64_t* tile_base,
+                 const uint32_t* tile_seg, uint32_t n_tiles, int k, int shift, uint32_t* tile_ctr,
+                 uint32_t* sub_cnt, uint64_t* cursor, const uint64_t* sub_end, void* keys, int* err, int grid,
+                 cudaStream_t st);
+uint32_t local_cap(int key_words);
+uint32_t local_cap_big(int key_words);
+void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, bool big, int shift0,
+                       int key_words, void* keys, uint32_t* kcount, uint32_t* kc, uint32_t* ov_list,
+                       uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
+                       uint32_t* max_count, uint64_t* n_distinct, uint32_t* claim, int* err, int num_sms,
+                       cudaStream_t st);
+void launch_compact(const uint64_t* sub_off, const uint32_t* kc, const uint64_t* out_off, uint32_t n_sub,
+                    int key_words, const void* keys, const uint32_t* kcount, void* out_keys, uint32_t* out_counts,
+                    uint64_t out_cap, int* err, int grid, cudaStream_t st);
+void launch_ov_gather(const uint64_t* sub_off, const uint32_t* ov_list, uint32_t n_ov, uint64_t* ov_pre,
+                      int key_words, const void* keys, void* dst, uint64_t dst_cap, int* err, int grid,
+                      cudaStream_t st);
+
 uint64_t rle_tiles(uint64_t n, int key_words);
 uint64_t rle_bits_words(uint64_t n);
 // Pass 1: head bitmask, per-tile first/last head and kept count of the runs

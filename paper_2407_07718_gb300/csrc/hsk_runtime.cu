@@ -44,21 +44,6 @@ void hsk_set_error(hsk_ctx* c, const char* fmt, ...) {
     if (c) c->err_msg = buf;
 }
 
-#define CK(call)                                                                            \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess) {                                                            \
-            hsk_set_error(c, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
-                          __FILE__, __LINE__);                                              \
-            return HSK_ECUDA;                                                               \
-        }                                                                                   \
-    } while (0)
-
-#define TRY(x)                      \
-    do {                            \
-        int rc_ = (x);              \
-        if (rc_ != HSK_OK) return rc_; \
-    } while (0)
 
 int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new) {
     if (bytes == 0) bytes = 256;
@@ -151,6 +136,7 @@ extern "C" int hsk_config_default(hsk_config* cfg) {
     cfg->max_chunk_kmers = 0;
     cfg->seed = 0x9E3779B97F4A7C15ULL;
     cfg->autotune = 1;
+    cfg->local_sort = 1;
     return HSK_OK;
 }
 
@@ -187,6 +173,8 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
     c->d_nheads = (uint64_t*)(s + 16);
     c->d_nout = (uint64_t*)(s + 24);
     c->d_ndesc = (uint64_t*)(s + 32);
+    c->d_nlocal = (uint64_t*)(s + 40);
+    c->d_ovstats = (uint64_t*)(s + 48);
     c->counters = (uint32_t*)(s + 256);
     *out = c;
     return HSK_OK;
@@ -216,6 +204,7 @@ extern "C" int hsk_debug_fail_alloc_after(hsk_ctx* c, int n) {
 }
 
 extern "C" uint64_t hsk_debug_allocated(hsk_ctx* c) { return c ? c->allocated : 0; }
+extern "C" uint64_t hsk_debug_last_overflow(hsk_ctx* c) { return c ? c->last_ov_keys : 0; }
 
 // ---------------------------------------------------------------------------
 // launch counter and stage profiling
@@ -299,10 +288,14 @@ static int check_args(hsk_ctx* c, const void* reads, const void* offsets, uint64
     return HSK_OK;
 }
 
-static int read_device_error(hsk_ctx* c, cudaStream_t st) {
-    int derr = 0;
-    CK(cudaMemcpyAsync(&derr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+// Reads the device error word (and the largest count, stored 8 bytes after it)
+// once the stream's work is done.
+static int read_device_error(hsk_ctx* c, cudaStream_t st, uint32_t* max_count = nullptr) {
+    uint32_t w[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(w, c->d_err, sizeof(w), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    const int derr = (int)w[0];
+    if (max_count) *max_count = w[2];
     if (derr == HSK_DERR_OFFSETS) {
         hsk_set_error(c, "offsets must start at 0, be non-decreasing and end at n_bases");
         return HSK_EINVAL;
@@ -342,11 +335,13 @@ int hsk_encode_into(hsk_ctx* c, const char* d_reads, uint64_t n_bases, const uin
     return HSK_OK;
 }
 
-uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases) {
+uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k) {
     if (c->cfg.n_buckets) return c->cfg.n_buckets;
     // small jobs: fewer buckets keep the per-CTA tables cheap
     if (n_bases < (1ull << 22)) return 256;
-    return 4096;
+    // 128-bit keys: the on-chip sort holds half as many keys per sub-segment,
+    // so large jobs need twice the groups
+    return (k > 32 && c->cfg.local_sort) ? 8192 : 4096;
 }
 
 static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, SmParams& P) {
@@ -441,6 +436,25 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
 }
 
 static int n_passes_for(int key_bits) { return (key_bits + 7) / 8; }
+
+// Output capacity for `need` pairs; the pairs already there are kept.
+static int grow_output(hsk_ctx* c, const Output& O, uint64_t need, int key_words, cudaStream_t st) {
+    const size_t kb = (size_t)key_words * 8;
+    if (c->out_keys.cap >= need * kb && c->out_counts.cap >= need * 4) return HSK_OK;
+    DevBuf nk, ncn;
+    TRY(hsk_ensure(c, nk, need * kb + need * kb / 4, false));
+    TRY(hsk_ensure(c, ncn, need * 4 + need, false));
+    if (O.n_pairs) {
+        CK(cudaMemcpyAsync(nk.p, c->out_keys.p, O.n_pairs * kb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ncn.p, c->out_counts.p, O.n_pairs * 4, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    free_buf(c, c->out_keys);
+    free_buf(c, c->out_counts);
+    c->out_keys = nk;
+    c->out_counts = ncn;
+    return HSK_OK;
+}
 
 // C zeroed tile counters in a row for one launch.
 static int next_counters(hsk_ctx* c, cudaStream_t st, uint32_t n, uint32_t** ctr) {
@@ -555,23 +569,8 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
     CK(cudaMemcpyAsync(&kept, t_off + nt, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     O.n_distinct += D;
-    // output capacity: previous pairs + the kept ones (grown with copy)
     const size_t kb = (size_t)key_words * 8;
-    const uint64_t need = O.n_pairs + kept;
-    if (c->out_keys.cap < need * kb || c->out_counts.cap < need * 4) {
-        DevBuf nk, ncn;
-        TRY(hsk_ensure(c, nk, need * kb + need * kb / 4, false));
-        TRY(hsk_ensure(c, ncn, need * 4 + need, false));
-        if (O.n_pairs) {
-            CK(cudaMemcpyAsync(nk.p, c->out_keys.p, O.n_pairs * kb, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(ncn.p, c->out_counts.p, O.n_pairs * 4, cudaMemcpyDeviceToDevice, st));
-            CK(cudaStreamSynchronize(st));
-        }
-        free_buf(c, c->out_keys);
-        free_buf(c, c->out_counts);
-        c->out_keys = nk;
-        c->out_counts = ncn;
-    }
+    TRY(grow_output(c, O, O.n_pairs + kept, key_words, st));
     launch_rle_write(sorted, n, key_words, (const uint32_t*)c->heads.p, t_next, t_off, lo, hi,
                      (char*)c->out_keys.p + O.n_pairs * kb, (uint32_t*)c->out_counts.p + O.n_pairs, kept,
                      c->d_err, c->num_sms * 4, st);
@@ -640,6 +639,122 @@ int hsk_plan_chunks(hsk_ctx* c, const Supermers& S, int key_words,
     return HSK_OK;
 }
 
+// One chunk of buckets through the on-chip path.  The buckets are cut into C
+// groups (cut[0..C]); every group's keys are split by their top digit into
+// 256 sub-segments, each sorted and counted in shared memory (k_local.cu);
+// sub-segments over capacity go through the global radix passes and S5.  The
+// kept pairs are appended to the output unordered (stage S6 orders them).
+static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_t>& cut, uint64_t nk, int k,
+                       uint32_t lo, uint32_t hi, uint32_t H, Output& O, cudaStream_t st) {
+    const int kw = k <= 32 ? 1 : 2;
+    const size_t kb = (size_t)kw * 8;
+    const uint32_t C = (uint32_t)cut.size() - 1;
+    const uint64_t NS = (uint64_t)C * 256;
+    const int key_bits = 2 * k;
+    const int shift0 = key_bits > 8 ? key_bits - 8 : 0;
+    // record range and record tiles of each group; the tile -> group map
+    std::vector<uint64_t> rbase(C + 1), tbase(C + 1);
+    uint64_t nt = 0;
+    for (uint32_t i = 0; i <= C; ++i) rbase[i] = S.h_bucket_rec[cut[i]];
+    for (uint32_t i = 0; i < C; ++i) {
+        tbase[i] = nt;
+        nt += expand_tiles(rbase[i + 1] - rbase[i]);
+    }
+    tbase[C] = nt;
+    if (nt >= 0xFFFFFFFFull) {
+        hsk_set_error(c, "%llu record tiles in one chunk", (unsigned long long)nt);
+        return HSK_EOVERFLOW;
+    }
+    std::vector<uint32_t> tseg(nt);
+    for (uint32_t i = 0; i < C; ++i)
+        for (uint64_t t = tbase[i]; t < tbase[i + 1]; ++t) tseg[t] = i;
+    TRY(hsk_ensure(c, c->keys, nk * kb, false));
+    TRY(hsk_ensure(c, c->alt, nk * 4, false));  // counts of the kept pairs
+    // sub-segment tables: sub_cnt | kc | ov_list | ov_list2 (u32[NS] each),
+    // then sub_off (NS + 1) | cursor (NS) | kc_off (NS + 1) (u64)
+    const size_t t32 = 4 * NS * 4;
+    TRY(hsk_ensure(c, c->loc_tab, t32 + (3 * NS + 2) * 8, false));
+    uint32_t* sub_cnt = (uint32_t*)c->loc_tab.p;
+    uint32_t* kcv = sub_cnt + NS;
+    uint32_t* ov_list = kcv + NS;
+    uint32_t* ov_list2 = ov_list + NS;
+    uint64_t* sub_off = (uint64_t*)((char*)c->loc_tab.p + t32);
+    uint64_t* cursor = sub_off + NS + 1;
+    uint64_t* kc_off = cursor + NS;
+    TRY(hsk_ensure(c, c->batch_d, std::max<uint64_t>(nt, 1) * 4, false));
+    TRY(upload_segments(c, rbase, &tbase, st));
+    if (nt) CK(cudaMemcpyAsync(c->batch_d.p, tseg.data(), nt * 4, cudaMemcpyHostToDevice, st));
+    const uint64_t* d_rbase = (const uint64_t*)c->seg.p;
+    const uint64_t* d_tbase = d_rbase + (C + 1);
+    const uint32_t* d_tseg = (const uint32_t*)c->batch_d.p;
+    // count keys per (group, top digit), offsets, scatter
+    CK(cudaMemsetAsync(sub_cnt, 0, NS * 4, st));
+    uint32_t *ctr, ep;
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_part(0, S.records, d_rbase, d_tbase, d_tseg, (uint32_t)nt, k, shift0, ctr, sub_cnt, nullptr, nullptr,
+                nullptr, c->d_err, expand_grid(c->num_sms), st);
+    TRY(ensure_status(c, scan_status_words(NS), st));
+    TRY(hsk_next_epoch(c, st, &ep));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_scan_u32(sub_cnt, NS, sub_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    CK(cudaMemcpyAsync(cursor, sub_off, NS * 8, cudaMemcpyDeviceToDevice, st));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_part(1, S.records, d_rbase, d_tbase, d_tseg, (uint32_t)nt, k, shift0, ctr, nullptr, cursor,
+                sub_off + 1, c->keys.p, c->d_err, expand_grid(c->num_sms), st);
+    CK(cudaGetLastError());
+    prof_mark(c, st, 3);
+    // sort and count on chip; the sub-segments that do not fit go to a second
+    // pass with three times the capacity, and what fits neither to the
+    // global radix passes
+    CK(cudaMemsetAsync(c->d_nlocal, 0, 40, st));  // distinct, pass-1 and pass-2 overflow stats
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_local_sort(sub_off, nullptr, (uint32_t)NS, false, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
+                      ov_list, c->d_ovstats, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, ctr, c->d_err,
+                      c->num_sms, st);
+    CK(cudaGetLastError());
+    uint64_t st5[5] = {0, 0, 0, 0, 0};  // distinct, pass-1 {listed, keys}, pass-2 {listed, keys}
+    CK(cudaMemcpyAsync(st5, c->d_nlocal, 24, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t n_ov1 = (uint32_t)(st5[1] & 0xFFFFFFFFull);
+    if (n_ov1) {
+        TRY(hsk_next_counter(c, st, &ctr));
+        launch_local_sort(sub_off, ov_list, n_ov1, true, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
+                          ov_list2, c->d_ovstats + 2, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, ctr,
+                          c->d_err, c->num_sms, st);
+        CK(cudaGetLastError());
+    }
+    TRY(hsk_next_epoch(c, st, &ep));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_scan_u32(kcv, NS, kc_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    CK(cudaGetLastError());
+    prof_mark(c, st, 4);
+    uint64_t kept = 0;
+    CK(cudaMemcpyAsync(st5, c->d_nlocal, sizeof(st5), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&kept, kc_off + NS, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t n_ov = (uint32_t)(st5[3] & 0xFFFFFFFFull);
+    const uint64_t ov_keys = st5[4];
+    O.n_distinct += st5[0];
+    TRY(grow_output(c, O, O.n_pairs + kept, kw, st));
+    launch_compact(sub_off, kcv, kc_off, (uint32_t)NS, kw, c->keys.p, (const uint32_t*)c->alt.p,
+                   (char*)c->out_keys.p + O.n_pairs * kb, (uint32_t*)c->out_counts.p + O.n_pairs, kept, c->d_err,
+                   c->num_sms * 8, st);
+    CK(cudaGetLastError());
+    O.n_pairs += kept;
+    if (n_ov) {  // the sub-segments that did not fit: global radix passes, then S5
+        TRY(hsk_ensure(c, c->batch_a, ov_keys * kb, false));
+        TRY(hsk_ensure(c, c->batch_c, ((uint64_t)n_ov + 1) * 8, false));
+        launch_ov_gather(sub_off, ov_list2, n_ov, (uint64_t*)c->batch_c.p, kw, c->keys.p, c->batch_a.p, ov_keys,
+                         c->d_err, c->num_sms * 4, st);
+        CK(cudaGetLastError());
+        TRY(plain_sort(c, c->batch_a.p, nullptr, ov_keys, kw, key_bits, c->batch_b, nullptr, st));
+        TRY(hsk_rle_chunk(c, c->batch_a.p, ov_keys, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
+    }
+    c->last_ov_keys += ov_keys;
+    prof_mark(c, st, 5);
+    return HSK_OK;
+}
+
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
                   DevResult& R) {
@@ -665,7 +780,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
     prof_mark(c, st, 0);
     Supermers S;
-    uint32_t B = hsk_pick_buckets(c, n_bases);
+    uint32_t B = hsk_pick_buckets(c, n_bases, k);
     TRY(hsk_supermers(c, E, k, m, B, S, st));
     prof_mark(c, st, 2);
     R.n_windows = S.n_kmers;
@@ -674,10 +789,21 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     if (S.n_kmers > 0) TRY(hsk_plan_chunks(c, S, kw, chunks));
     const int P = n_passes_for(2 * k);
     uint32_t total_segments = 0;
+    bool unordered = false;
+    c->last_ov_keys = 0;
     for (auto& ch : chunks) {
         uint64_t nk = 0;
         for (uint32_t b = ch.first; b < ch.second; ++b) nk += S.h_bucket_kmers[b];
         if (nk == 0) continue;
+        if (c->cfg.local_sort) {
+            // groups of about a third of the on-chip capacity per top digit
+            const uint64_t per_group = 256ull * local_cap(kw) / 3;
+            const uint32_t C_want = (uint32_t)std::min<uint64_t>(ch.second - ch.first,
+                                                                 std::max<uint64_t>(1, nk / per_group));
+            TRY(local_chunk(c, S, group_buckets(S, ch.first, ch.second, C_want), nk, k, lo, hi, H, O, st));
+            unordered = true;
+            continue;
+        }
         // segments: groups of buckets sorted independently, tiles interleaved
         uint32_t C_want = (uint32_t)std::min<uint64_t>({(uint64_t)HSK_SEGMENTS, ch.second - ch.first,
                                                         std::max<uint64_t>(1, nk / HSK_MIN_SEGMENT_KMERS)});
@@ -724,14 +850,13 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
         TRY(hsk_rle_chunk(c, sorted, nk, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
         prof_mark(c, st, 5);
     }
-    if (total_segments > 1)
+    if (total_segments > 1 || unordered)
         TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st));
     prof_mark(c, st, 6);
     CK(cudaEventRecord(c->ev1, st));
-    TRY(read_device_error(c, st));
-    prof_collect(c);
     uint32_t mx = 0;
-    CK(cudaMemcpy(&mx, c->d_max, 4, cudaMemcpyDeviceToHost));
+    TRY(read_device_error(c, st, &mx));
+    prof_collect(c);
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     R.n_pairs = O.n_pairs;
@@ -961,9 +1086,8 @@ extern "C" int hsk_stage_rle(hsk_ctx* c, const uint64_t* d_sorted, uint64_t n, i
     c->ctr_used = 0;
     Output O;
     TRY(hsk_rle_chunk(c, d_sorted, n, key_words, lo, hi, H, (uint64_t*)c->hist.p, O, st));
-    TRY(read_device_error(c, st));
     uint32_t mx = 0;
-    CK(cudaMemcpy(&mx, c->d_max, 4, cudaMemcpyDeviceToHost));
+    TRY(read_device_error(c, st, &mx));
     DevResult R;
     memset(&R, 0, sizeof R);
     R.n_pairs = O.n_pairs;

@@ -16,8 +16,8 @@
 
 #include "../../include/hsk.h"
 
-#define HSK_N_COUNTERS 1024
-#define HSK_SMALL_BYTES 8192
+#define HSK_N_COUNTERS 16384
+#define HSK_SMALL_BYTES (256 + HSK_N_COUNTERS * 4)
 #define HSK_MAX_BUCKETS 8192
 #ifndef HSK_SEGMENTS
 #define HSK_SEGMENTS 256            // bucket groups sorted side by side
@@ -63,11 +63,29 @@ struct DevResult {
     double device_ms;
 };
 
+// Host array whose elements are left uninitialised on resize: a device copy
+// fills them at once, so zero-filling hundreds of MB first would be wasted.
+template <class T>
+struct HostArr {
+    std::unique_ptr<T[]> p;
+    size_t n = 0, cap = 0;
+    void resize(size_t m) {
+        if (m > cap) {
+            p.reset(new T[m]);
+            cap = m;
+        }
+        n = m;
+    }
+    T* data() { return p.get(); }
+    const T* data() const { return p.get(); }
+    size_t size() const { return n; }
+};
+
 struct HostResult {
     DevResult R{};
-    std::vector<uint64_t> kmers;
-    std::vector<uint32_t> counts;
-    std::vector<uint64_t> hist;
+    HostArr<uint64_t> kmers;
+    HostArr<uint32_t> counts;
+    HostArr<uint64_t> hist;
 };
 
 struct ServeState;  // served form (hsk_serve.cu)
@@ -89,6 +107,8 @@ struct hsk_ctx {
     uint64_t* d_nheads = nullptr;
     uint64_t* d_nout = nullptr;
     uint64_t* d_ndesc = nullptr;
+    uint64_t* d_nlocal = nullptr;   // distinct k-mers counted on chip
+    uint64_t* d_ovstats = nullptr;  // [0] low half: sub-segments sent to the global path, [1] their keys
     uint32_t* counters = nullptr;
     uint32_t ctr_used = 0;
     uint32_t epoch = 0;
@@ -100,7 +120,8 @@ struct hsk_ctx {
     DevBuf keys, alt, pass_hist, digit_off, lb_status, seg;        // S4
     DevBuf heads, rle_tiles, out_keys, out_counts, hist;           // S5
     DevBuf pair_alt_keys, pair_alt_counts;                         // S6
-    DevBuf batch_a, batch_b, batch_c, batch_d;                     // batched form
+    DevBuf loc_tab;                                                // on-chip path: sub-segment tables
+    DevBuf batch_a, batch_b, batch_c, batch_d;                     // on-chip path: overflow keys, tile map
 
     void* h_pin = nullptr;
     size_t h_pin_cap = 0;
@@ -116,16 +137,34 @@ struct hsk_ctx {
     std::vector<std::pair<int, int>> marks;  // (event index, stage id; -1 = start)
     double prof_ms[8] = {0};
     uint64_t prof_passes = 0;
+    uint64_t last_ov_keys = 0;  // keys of the last job that did not fit the on-chip sort
 
     std::vector<DevBuf*> all_bufs() {
         return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
                 &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads, &rle_tiles,
-                &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &batch_a,
+                &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &loc_tab, &batch_a,
                 &batch_b, &batch_c, &batch_d};
     }
 };
 
 void hsk_set_error(hsk_ctx* c, const char* fmt, ...);
+
+// CUDA call / library call checks for functions with an hsk_ctx* c in scope
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            hsk_set_error(c, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
+                          __FILE__, __LINE__);                                              \
+            return HSK_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)
+
+#define TRY(x)                      \
+    do {                            \
+        int rc_ = (x);              \
+        if (rc_ != HSK_OK) return rc_; \
+    } while (0)
 int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new);
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,

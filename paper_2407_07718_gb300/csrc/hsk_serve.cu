@@ -8,8 +8,8 @@
 // budget next to what the other slots hold; idle slots give their arenas back
 // when a job would not fit otherwise.  Jobs complete in any order.
 //
-// Batched form: hsk_count_batch runs many independent read sets; see
-// hsk_batch.cu for the packed path.
+// Batched form: hsk_count_batch queues many independent read sets on the same
+// slots, largest first, and returns when all are done.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -303,7 +303,7 @@ extern "C" int hsk_ticket_times(hsk_ctx* c, uint64_t ticket, double* queued_s, d
 }
 
 // ---------------------------------------------------------------------------
-// batched form (first version: one context, jobs in order)
+// batched form: the jobs go through the serving slots, largest first
 // ---------------------------------------------------------------------------
 extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs, hsk_result* outs) {
     if (!c || (n_jobs && (!jobs || !outs))) return HSK_EINVAL;
@@ -311,14 +311,52 @@ extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs,
         int rc = validate_job(c, jobs + i);
         if (rc != HSK_OK) return rc;
     }
-    cudaSetDevice(c->cfg.device);
+    CK(cudaSetDevice(c->cfg.device));
     c->batch_res.clear();
     c->batch_res.resize(n_jobs);
-    for (uint32_t i = 0; i < n_jobs; ++i) {
-        const hsk_job& j = jobs[i];
-        int rc = hsk_count_host_on(c, j.reads, j.offsets, j.n_reads, j.k, j.m, j.lo, j.hi, c->stream,
-                                   c->in_reads, c->in_offsets, c->batch_res[i]);
-        if (rc != HSK_OK) return rc;
+    if (n_jobs == 0) return HSK_OK;
+    TRY(serve_start(c));
+    ServeState* S = c->serve;
+    // Largest job first (longest-processing-time order): with the slots
+    // running side by side, the big jobs start early and the small ones fill
+    // the gaps, which shortens the makespan.
+    std::vector<uint32_t> order(n_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) order[i] = i;
+    auto bases = [&](uint32_t i) { return jobs[i].n_reads ? jobs[i].offsets[jobs[i].n_reads] : 0; };
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return bases(a) > bases(b); });
+    std::vector<uint64_t> ids(n_jobs);
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        for (uint32_t i : order) {
+            auto T = std::make_unique<Ticket>();
+            T->job = jobs[i];
+            T->est = job_estimate(jobs[i]);
+            T->t_submit = now_s();
+            uint64_t id = S->next_ticket++;
+            S->tickets[id] = std::move(T);
+            S->queue.push_back(id);
+            ids[i] = id;
+        }
+    }
+    S->cv_work.notify_all();
+    int first_rc = HSK_OK;
+    std::string first_err;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        for (uint32_t i = 0; i < n_jobs; ++i) {
+            Ticket* T = S->tickets[ids[i]].get();
+            S->cv_done.wait(lk, [&] { return T->state == T_DONE; });
+            if (T->rc != HSK_OK && first_rc == HSK_OK) {
+                first_rc = T->rc;
+                first_err = "job " + std::to_string(i) + ": " + T->err;
+            }
+            c->batch_res[i] = std::move(T->res);
+            S->tickets.erase(ids[i]);
+        }
+    }
+    if (first_rc != HSK_OK) {
+        c->err_msg = first_err;
+        return first_rc;
     }
     for (uint32_t i = 0; i < n_jobs; ++i) fill_out(c->batch_res[i], outs + i);
     return HSK_OK;

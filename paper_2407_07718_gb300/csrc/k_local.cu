@@ -1,0 +1,778 @@
+// k_local.cu -- stage S4 + S5 on chip: each minimizer-bucket group is cut by
+// the top digit of its keys into 256 sub-segments, and every sub-segment that
+// fits shared memory is sorted, run-length counted, histogrammed and filtered
+// by one CTA without going back to HBM.
+//
+// The paper's tasks (Sec. 3.4) are independent groups of k-mers that each
+// worker sorts on its own and then counts with one linear scan (Sec. 3.1).
+// Here the tasks are cut fine enough to fit an SM: a bucket group never shares
+// a k-mer value with another group, and within a group keys with different
+// top digits differ, so every (group, top digit) sub-segment can be sorted and
+// counted alone.  The global onesweep passes (k_sort.cu) stay as the path for
+// sub-segments that do not fit.
+//
+//   k_part<MODE 0> -- supermer records -> key count per (group, top digit).
+//   k_part<MODE 1> -- supermer records -> keys scattered to their
+//                     sub-segments (a tile's keys are grouped by digit in
+//                     shared memory first, so the writes are runs; the order
+//                     inside a sub-segment is free, the sub-segment sort fixes it).
+//   k_local_sort   -- per sub-segment: load into shared memory, MSD radix
+//                     partitions (an 11-bit digit, then 8-bit digits where a
+//                     bin stays large), runs counted inside each bin (key by
+//                     key in small bins, by one warp peeling off distinct keys
+//                     in larger ones), histogram, [lo, hi] filter; kept
+//                     (key, count) pairs written at the start of the
+//                     sub-segment's own range.  A second launch with one CTA
+//                     per SM and three times the capacity takes the
+//                     sub-segments that did not fit; what fits neither is
+//                     listed for the global path.
+//   k_compact      -- kept pairs of all sub-segments -> one output array.
+//   k_ov_gather    -- the listed sub-segments' keys -> one array for the
+//                     global path.
+#include "hsk_device.cuh"
+
+namespace hsk {
+
+constexpr int LP_NT = 256;
+
+// ---------------------------------------------------------------------------
+// partition by top digit (count, then scatter)
+// ---------------------------------------------------------------------------
+template <bool WIDE>
+struct PartCfg {
+    static constexpr int ROUND = WIDE ? 2048 : 4096;  // keys grouped per scatter round
+    static constexpr int IPT = ROUND / LP_NT;
+};
+
+size_t part_smem_bytes(int mode, int k) {
+    const bool wide = k > 32;
+    const size_t rec = (size_t)EXP_TILE * (wide ? 4 : 2) * 8;
+    if (mode == 0) return rec;
+    return rec + (size_t)(wide ? PartCfg<true>::ROUND * 16 : PartCfg<false>::ROUND * 8);
+}
+
+// Work: one counter over all record tiles of all groups; tile g belongs to
+// group tile_seg[g] and is tile g - tile_base[group] of it.
+// MODE 0: sub_cnt[c * 256 + d] += keys of group c whose digit at `shift` is d.
+// MODE 1: every key to keys_out[cursor[c * 256 + d]++] (a reservation per
+//         digit and round), never past sub_end[c * 256 + d].
+template <bool WIDE, int MODE>
+__global__ void __launch_bounds__(LP_NT) k_part(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
+                                                const u64* __restrict__ tile_base, const uint32_t* __restrict__ tile_seg,
+                                                uint32_t n_tiles, int k, int shift, uint32_t* tile_ctr,
+                                                uint32_t* __restrict__ sub_cnt, unsigned long long* cursor,
+                                                const u64* __restrict__ sub_end, void* __restrict__ keys_out,
+                                                int* err) {
+    using K = typename std::conditional<WIDE, key128, u64>::type;
+    constexpr int RW = WIDE ? 4 : 2;
+    constexpr int ROUND = PartCfg<WIDE>::ROUND, IPT = PartCfg<WIDE>::IPT;
+    extern __shared__ __align__(16) u64 smem_part[];
+    u64* s_rec = smem_part;                                         // EXP_TILE * RW words
+    K* s_keys = reinterpret_cast<K*>(smem_part + EXP_TILE * RW);    // ROUND keys (MODE 1)
+    __shared__ uint32_t s_pre[EXP_TILE + 1];
+    __shared__ uint32_t s_cnt[256], s_fill[256], s_dstart[256];
+    __shared__ u64 s_gbase[256];
+    __shared__ u64 s_scr[9];
+    __shared__ uint32_t s_scr32[9];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x;
+    if (MODE == 0) s_cnt[tid] = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const uint32_t g = s_tile;
+        if (g >= n_tiles) break;
+        const uint32_t c = tile_seg[g];
+        const u64 tile = g - tile_base[c];
+        const u64 rb = rec_base[c], n_rec = rec_base[c + 1] - rb;
+        const u64 r0 = tile * EXP_TILE;
+        const uint32_t nr = (uint32_t)(n_rec - r0 < (u64)EXP_TILE ? n_rec - r0 : (u64)EXP_TILE);
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rec + (rb + r0) * RW);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rec);
+        for (uint32_t i = tid; i < nr * (RW / 2); i += LP_NT) dst[i] = src[i];
+        __syncthreads();
+        uint32_t nk[EXP_RPT], sum = 0;
+#pragma unroll
+        for (int i = 0; i < EXP_RPT; ++i) {
+            const uint32_t r = tid * EXP_RPT + i;
+            nk[i] = r < nr ? (uint32_t)(s_rec[r * RW + RW - 1] & 0xFF) : 0u;
+            sum += nk[i];
+        }
+        u64 total;
+        const u64 excl = block_excl_sum<LP_NT, u64>((u64)sum, s_scr, total);
+        {
+            uint32_t run = (uint32_t)excl;
+#pragma unroll
+            for (int i = 0; i < EXP_RPT; ++i) {
+                s_pre[tid * EXP_RPT + i] = run;
+                run += nk[i];
+            }
+            if (tid == LP_NT - 1) s_pre[EXP_TILE] = run;
+        }
+        __syncthreads();
+        const uint32_t T = (uint32_t)total;
+        if (MODE == 0) {
+            for (uint32_t j = tid; j < T; j += LP_NT) {
+                const K key = tile_key<WIDE>(s_rec, s_pre, nr, j, k);
+                atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u);
+            }
+            __syncthreads();
+            const uint32_t v = s_cnt[tid];
+            if (v) atomicAdd(sub_cnt + (u64)c * 256 + tid, v);
+            s_cnt[tid] = 0;
+        } else {
+            K* out = reinterpret_cast<K*>(keys_out);
+            for (uint32_t j0 = 0; j0 < T; j0 += ROUND) {
+                const uint32_t nround = T - j0 < (uint32_t)ROUND ? T - j0 : (uint32_t)ROUND;
+                s_cnt[tid] = 0;
+                __syncthreads();
+                K kk[IPT];
+                uint32_t dd[IPT];
+#pragma unroll
+                for (int i = 0; i < IPT; ++i) {
+                    const uint32_t j = (uint32_t)i * LP_NT + tid;
+                    if (j < nround) {
+                        kk[i] = tile_key<WIDE>(s_rec, s_pre, nr, j0 + j, k);
+                        dd[i] = key_digit(kk[i], shift, 0xFF);
+                        atomicAdd(&s_cnt[dd[i]], 1u);
+                    }
+                }
+                __syncthreads();
+                const uint32_t cnt = s_cnt[tid];
+                uint32_t tot;
+                const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, tot);
+                s_dstart[tid] = ex;
+                s_fill[tid] = ex;
+                if (cnt) {
+                    const u64 slot = (u64)c * 256 + tid;
+                    u64 at = atomicAdd(cursor + slot, (unsigned long long)cnt);
+                    if (at + cnt > sub_end[slot]) {
+                        raise_error(err, HSK_DERR_BOUNDS);
+                        at = ~0ULL;
+                    }
+                    s_gbase[tid] = at;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < IPT; ++i) {
+                    const uint32_t j = (uint32_t)i * LP_NT + tid;
+                    if (j < nround) s_keys[atomicAdd(&s_fill[dd[i]], 1u)] = kk[i];
+                }
+                __syncthreads();
+                for (uint32_t i = tid; i < nround; i += LP_NT) {
+                    const K key = s_keys[i];
+                    const uint32_t d = key_digit(key, shift, 0xFF);
+                    const u64 at = s_gbase[d];
+                    if (at != ~0ULL) out[at + (i - s_dstart[d])] = key;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+void launch_part(int mode, const uint64_t* records, const uint64_t* rec_base, const uint64_t* tile_base,
+                 const uint32_t* tile_seg, uint32_t n_tiles, int k, int shift, uint32_t* tile_ctr,
+                 uint32_t* sub_cnt, uint64_t* cursor, const uint64_t* sub_end, void* keys, int* err, int grid,
+                 cudaStream_t st) {
+    if (n_tiles == 0) return;
+    count_launch();
+    unsigned g = n_tiles < (uint32_t)grid ? n_tiles : (unsigned)grid;
+    if (g < 1) g = 1;
+    const size_t dyn = part_smem_bytes(mode, k);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        kern<<<g, LP_NT, dyn, st>>>((const u64*)records, (const u64*)rec_base, (const u64*)tile_base, tile_seg,
+                                    n_tiles, k, shift, tile_ctr, sub_cnt, (unsigned long long*)cursor,
+                                    (const u64*)sub_end, keys, err);
+    };
+    if (k <= 32) {
+        if (mode == 0) go(k_part<false, 0>);
+        else go(k_part<false, 1>);
+    } else {
+        if (mode == 0) go(k_part<true, 0>);
+        else go(k_part<true, 1>);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sort + count one sub-segment in shared memory
+// ---------------------------------------------------------------------------
+// Capacity of one CTA's two shared-memory key buffers.  The first pass runs
+// 3 CTAs per SM; the second takes the sub-segments that did not fit, one CTA
+// per SM with most of the SM's shared memory.  STACK and LIST bound the open
+// bins (disjoint, > LS_MED keys each) and the bins over LS_SMALL keys.
+template <typename K, bool BIG>
+struct LocalCfg;
+template <>
+struct LocalCfg<u64, false> {
+    static constexpr int CAP = 4096, STACK = 16, LIST = 256;  // 2 x 32 KB
+};
+template <>
+struct LocalCfg<key128, false> {
+    static constexpr int CAP = 2048, STACK = 16, LIST = 128;  // 2 x 32 KB
+};
+template <>
+struct LocalCfg<u64, true> {
+    static constexpr int CAP = 12288, STACK = 48, LIST = 736;  // 2 x 96 KB
+};
+template <>
+struct LocalCfg<key128, true> {
+    static constexpr int CAP = 6144, STACK = 24, LIST = 368;   // 2 x 96 KB
+};
+constexpr int LS_D1 = 11;          // bits of the first partition's digit
+constexpr int LS_B1 = 1 << LS_D1;  // its bins (8 consecutive bins per thread)
+constexpr int LS_SMALL = 16;       // bins of at most this many keys: counted key by key
+constexpr int LS_MED = 256;        // bins of at most this many keys: rank sort by one warp
+constexpr int LS_PEEL = 8;         // distinct keys peeled off a bin before it is sorted
+constexpr int LS_HS = 128;         // count-histogram bins kept in shared memory
+constexpr int LS_BATCH = 2;        // sub-segments claimed at once
+// open bins are disjoint and hold > LS_MED keys; listed bins hold > LS_SMALL
+#define HSK_LS_CHECK(K, BIG)                                                                        \
+    static_assert(LocalCfg<K, BIG>::CAP / (LS_MED + 1) < LocalCfg<K, BIG>::STACK, "stack too small"); \
+    static_assert(LocalCfg<K, BIG>::CAP / (LS_SMALL + 1) < LocalCfg<K, BIG>::LIST, "list too small")
+HSK_LS_CHECK(u64, false);
+HSK_LS_CHECK(u64, true);
+HSK_LS_CHECK(key128, false);
+HSK_LS_CHECK(key128, true);
+
+uint32_t local_cap(int key_words) {
+    return key_words == 1 ? LocalCfg<u64, false>::CAP : LocalCfg<key128, false>::CAP;
+}
+uint32_t local_cap_big(int key_words) {
+    return key_words == 1 ? LocalCfg<u64, true>::CAP : LocalCfg<key128, true>::CAP;
+}
+static size_t local_smem_bytes(int key_words, bool big) {
+    return (size_t)2 * (big ? local_cap_big(key_words) : local_cap(key_words)) * 8 * key_words;
+}
+
+struct LsBin {
+    uint32_t beg, len;
+    int shift, buf;  // digit of the next partition; buffer holding the bin (0 = A, 1 = B)
+};
+
+// Counting inside one sub-segment.  After the partitions, keys that are
+// equal share every digit and so one bin; a bin's runs are found without
+// ordering it: a key starts a run when no earlier key of the bin equals it,
+// and the run's count is the number of keys of the bin equal to it (bins of
+// <= LS_SMALL keys, one thread per key).  A warp takes larger bins by
+// peeling off one distinct key at a time (warp_bin); what is left after
+// LS_PEEL peels is rank-sorted and scanned, or, past LS_MED keys,
+// partitioned again on the next 8-bit digit by the whole CTA.  Every run
+// goes to `emit`.
+template <typename K, typename Emit>
+__device__ __forceinline__ void thread_bin(const K* v, uint32_t c, Emit& emit) {
+    for (uint32_t i = 0; i < c; ++i) {
+        const K x = v[i];
+        bool head = true;
+        uint32_t cnt = 0;
+        for (uint32_t j = 0; j < c; ++j)
+            if (key_eq(v[j], x)) {
+                ++cnt;
+                head = head && j >= i;
+            }
+        if (head) emit(x, cnt);
+    }
+}
+
+// A warp counts bin [sb, sb + len) of `src` (buffer src_buf; the same range
+// of `other` is free).  Peeling: the first remaining key's copies are
+// counted with one ballot pass over the bin and emitted, the other keys are
+// compacted into the other buffer, and so on -- a bin that holds a k-mer and
+// a few variants of it (sequencing errors past the digits already used) takes
+// one pass per distinct key.  The last <= 32 keys are counted lane-parallel.
+// After LS_PEEL peels the rest is rank-sorted and scanned (<= LS_MED keys) or
+// pushed for another partition.
+template <int STACK, typename K, typename Emit>
+__device__ __forceinline__ void warp_bin(K* src, K* other, uint32_t sb, uint32_t len, int next_shift, bool last_digit,
+                                         int src_buf, LsBin* stack, int* sp, int* abort_flag, int* err, Emit& emit) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    K* cur = src;
+    K* oth = other;
+    int cur_buf = src_buf;
+    uint32_t m = len;
+    for (int it = 0; m > 0; ++it) {
+        if (m <= 32) {
+            K x{};
+            bool head = false;
+            uint32_t cnt = 0;
+            if ((uint32_t)lane < m) {
+                x = cur[sb + lane];
+                head = true;
+                for (uint32_t j = 0; j < m; ++j)
+                    if (key_eq(cur[sb + j], x)) {
+                        ++cnt;
+                        head = head && j >= (uint32_t)lane;
+                    }
+            }
+            if (head) emit(x, cnt);
+            return;
+        }
+        if (it == LS_PEEL) break;
+        const K v = cur[sb];
+        uint32_t cnt = 0, kept = 0;
+        for (uint32_t i0 = 0; i0 < m; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool in = i < m;
+            const K x = in ? cur[sb + i] : v;
+            const bool eq = in && key_eq(x, v);
+            cnt += (uint32_t)__popc(__ballot_sync(0xffffffffu, eq));
+            const bool rest = in && !eq;
+            const uint32_t rm = __ballot_sync(0xffffffffu, rest);
+            if (rest) oth[sb + kept + (uint32_t)__popc(rm & lt)] = x;
+            kept += (uint32_t)__popc(rm);
+        }
+        if (lane == 0) emit(v, cnt);
+        __syncwarp();
+        K* t = cur;
+        cur = oth;
+        oth = t;
+        cur_buf ^= 1;
+        m = kept;
+    }
+    if (m <= (uint32_t)LS_MED) {  // many distinct keys left: rank sort into oth, then scan
+        for (uint32_t i = lane; i < m; i += 32) {
+            const K v = cur[sb + i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < m; ++j) {
+                const K u = cur[sb + j];
+                r += (key_lt(u, v) || (j < i && key_eq(u, v))) ? 1u : 0u;
+            }
+            oth[sb + r] = v;
+        }
+        __syncwarp();
+        const K* w = oth + sb;
+        for (uint32_t i = lane; i < m; i += 32) {
+            if (i > 0 && key_eq(w[i], w[i - 1])) continue;
+            uint32_t j = i + 1;
+            while (j < m && key_eq(w[j], w[i])) ++j;
+            emit(w[i], j - i);
+        }
+        __syncwarp();
+        return;
+    }
+    if (lane == 0) {
+        if (last_digit) {  // keys equal on every digit yet different: cannot happen
+            raise_error(err, HSK_DERR_BOUNDS);
+            *abort_flag = 1;
+        } else {
+            const int p = atomicAdd(sp, 1);
+            if (p < STACK) stack[p] = LsBin{sb, m, next_shift, cur_buf};
+            else *abort_flag = 1;
+        }
+    }
+}
+
+// Sub-segment s holds keys [sub_off[s], sub_off[s+1]) of `keys`; its top
+// digit (bits shift0 and up) is common to all of them.  The first partition
+// takes the next LS_D1 bits (count while loading, scan, scatter A -> B), so
+// a bin holds about one distinct key; each thread then counts its 8
+// consecutive bins, warps the larger ones.  Outputs: kc[s] kept pairs,
+// written to keys[sub_off[s] + i] and kcount[sub_off[s] + i], i < kc[s]
+// (in no particular order: stage S6 orders all pairs).  The counts of all
+// runs go to the histogram, their number to n_distinct, the largest to max_count.
+template <typename K, bool BIG>
+__global__ void __launch_bounds__(LP_NT) k_local_sort(const u64* __restrict__ sub_off,
+                                                      const uint32_t* __restrict__ only, uint32_t n_sub, int shift0,
+                                                      K* keys, uint32_t* __restrict__ kcount,
+                                                      uint32_t* __restrict__ kc, uint32_t* __restrict__ ov_list,
+                                                      unsigned long long* ov_stats, uint32_t lo, uint32_t hi,
+                                                      u64* __restrict__ hist, uint32_t hist_len,
+                                                      uint32_t* max_count, unsigned long long* n_distinct,
+                                                      uint32_t* claim, int* err) {
+    using Cfg = LocalCfg<K, BIG>;
+    constexpr int CAP = Cfg::CAP;
+    extern __shared__ __align__(16) unsigned char smem_local[];
+    K* A = reinterpret_cast<K*>(smem_local);
+    K* B = A + CAP;
+    // s_cnt1: first-partition counts, then cursors (= bin ends after the
+    // scatter); later its front holds the 8-bit partitions' counters/cursors
+    __shared__ uint32_t s_cnt1[LS_B1];
+    uint32_t* s_cnt = s_cnt1;              // [256]
+    uint32_t* s_cur = s_cnt1 + 256;        // [256]
+    __shared__ uint32_t s_list[Cfg::LIST]; // larger bins: start | length << 16
+    __shared__ uint32_t s_eqf[CAP / 32];   // key equals the first key of its (larger) bin
+    __shared__ uint32_t s_hist[LS_HS];
+    __shared__ LsBin s_stack[Cfg::STACK];
+    __shared__ uint32_t s_scr32[9];
+    __shared__ int s_sp, s_abort, s_nl;
+    __shared__ uint32_t s_kept, s_batch;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t hs = hist_len < (uint32_t)LS_HS ? hist_len : (uint32_t)LS_HS;
+    const int s1 = shift0 > LS_D1 ? shift0 - LS_D1 : 0;  // first partition's digit
+    const int s2 = s1 > 8 ? s1 - 8 : 0;                 // then 8-bit digits
+    for (int i = tid; i < LS_HS; i += LP_NT) s_hist[i] = 0;
+    u64 my_distinct = 0;
+    uint32_t my_max = 0, my_ones = 0;
+    u64 base = 0;
+    auto count_run = [&](uint32_t cnt) {
+        if (cnt == 1) {
+            ++my_ones;
+        } else {
+            const uint32_t b = cnt < hist_len - 1 ? cnt : hist_len - 1;
+            if (b < hs) atomicAdd(&s_hist[b], 1u);
+            else atomicAdd(reinterpret_cast<unsigned long long*>(hist + b), 1ULL);
+        }
+        ++my_distinct;
+        my_max = cnt > my_max ? cnt : my_max;
+    };
+    // one run, from a single lane
+    auto emit = [&](const K& key, uint32_t cnt) {
+        count_run(cnt);
+        if (cnt >= lo && cnt <= hi) {
+            const uint32_t p = atomicAdd(&s_kept, 1u);
+            keys[base + p] = key;
+            kcount[base + p] = cnt;
+        }
+    };
+    // runs of the lanes with head set, all lanes of the warp calling
+    auto emit_warp = [&](bool head, const K& key, uint32_t cnt) {
+        if (head) count_run(cnt);
+        const bool keep = head && cnt >= lo && cnt <= hi;
+        const uint32_t km = __ballot_sync(0xffffffffu, keep);
+        if (km) {
+            const int leader = __ffs(km) - 1;
+            uint32_t p0 = 0;
+            if (lane == leader) p0 = atomicAdd(&s_kept, (uint32_t)__popc(km));
+            p0 = __shfl_sync(0xffffffffu, p0, leader);
+            if (keep) {
+                const uint32_t p = p0 + (uint32_t)__popc(km & ((1u << lane) - 1u));
+                keys[base + p] = key;
+                kcount[base + p] = cnt;
+            }
+        }
+    };
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_batch = atomicAdd(claim, (uint32_t)LS_BATCH);
+        __syncthreads();
+        const uint32_t b0 = s_batch;
+        if (b0 >= n_sub) break;
+        const uint32_t b1 = b0 + LS_BATCH < n_sub ? b0 + LS_BATCH : n_sub;
+        for (uint32_t si = b0; si < b1; ++si) {
+            const uint32_t s = only ? only[si] : si;
+            base = sub_off[s];
+            const u64 n64 = sub_off[s + 1] - base;
+            if (n64 == 0) {
+                if (tid == 0) kc[s] = 0;
+                continue;
+            }
+            if (n64 > (u64)CAP) {
+                if (tid == 0) {
+                    kc[s] = 0;
+                    ov_list[atomicAdd(reinterpret_cast<unsigned int*>(ov_stats), 1u)] = s;
+                    atomicAdd(ov_stats + 1, (unsigned long long)n64);
+                }
+                continue;
+            }
+            const uint32_t n = (uint32_t)n64;
+            if (tid == 0) {
+                s_sp = 0;
+                s_abort = 0;
+                s_kept = 0;
+                s_nl = 0;
+            }
+            if (shift0 == 0) {  // the top digit is the whole key: one run
+                __syncthreads();
+                if (tid == 0) emit(keys[base], n);
+                __syncthreads();
+                if (tid == 0) kc[s] = s_kept;
+                continue;
+            }
+            // ---- first partition: load + count, scan, scatter A -> B
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s_cnt1[tid * 8 + j] = 0;
+            __syncthreads();
+            for (uint32_t i = tid; i < n; i += LP_NT) {
+                const K v = keys[base + i];
+                A[i] = v;
+                atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u);
+            }
+            __syncthreads();
+            uint32_t bc[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                bc[j] = s_cnt1[tid * 8 + j];
+                sum += bc[j];
+            }
+            uint32_t tot;
+            const uint32_t my0 = block_excl_sum<LP_NT, uint32_t>(sum, s_scr32, tot);
+            {
+                uint32_t run = my0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    s_cnt1[tid * 8 + j] = run;
+                    run += bc[j];
+                }
+            }
+            __syncthreads();
+            for (uint32_t i = tid; i < n; i += LP_NT) {
+                const K v = A[i];
+                B[atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u)] = v;
+            }
+            __syncthreads();
+            // ---- every key: its bin is [end of bin d-1, end of bin d); in a
+            // small bin, count the equal keys and emit at the first of them;
+            // the first key of a larger bin lists the bin for the warps
+            for (uint32_t i0 = 0; i0 < n; i0 += LP_NT) {
+                const uint32_t i = i0 + tid;
+                bool head = false, eqf = false;
+                uint32_t cnt = 0;
+                K v{};
+                if (i < n) {
+                    v = B[i];
+                    const uint32_t d = key_digit(v, s1, LS_B1 - 1);
+                    const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
+                    if (be - bs <= (uint32_t)LS_SMALL) {
+                        head = true;
+                        for (uint32_t j = bs; j < be; ++j)
+                            if (key_eq(B[j], v)) {
+                                ++cnt;
+                                head = head && j >= i;
+                            }
+                    } else {
+                        // larger bin: copies of its first key only mark the mask
+                        // (counted below); in bins of <= LS_MED keys every other
+                        // key counts its equals here, like a small bin's keys
+                        eqf = key_eq(v, B[bs]);
+                        if (!eqf && be - bs <= (uint32_t)LS_MED) {
+                            head = true;
+                            for (uint32_t j = bs; j < be; ++j)
+                                if (key_eq(B[j], v)) {
+                                    ++cnt;
+                                    head = head && j >= i;
+                                }
+                        }
+                        if (i == bs) s_list[atomicAdd(&s_nl, 1)] = bs | ((be - bs) << 16);
+                    }
+                }
+                const uint32_t fm = __ballot_sync(0xffffffffu, eqf);
+                if (lane == 0 && i0 + (uint32_t)warp * 32 < n) s_eqf[(i0 >> 5) + warp] = fm;
+                emit_warp(head, v, cnt);
+            }
+            __syncthreads();
+            {
+                const int nl = s_nl;
+                // bins of <= LS_MED keys: the first key's count is a popcount of the mask
+                for (int q = tid; q < nl; q += LP_NT) {
+                    const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
+                    if (len > (uint32_t)LS_MED) continue;
+                    uint32_t c1 = 0;
+                    for (uint32_t w = bs >> 5; w <= (be - 1) >> 5; ++w) {
+                        uint32_t m = s_eqf[w];
+                        if (w == bs >> 5) m &= 0xFFFFFFFFu << (bs & 31);
+                        if (w == (be - 1) >> 5 && ((be - 1) & 31) != 31) m &= (2u << ((be - 1) & 31)) - 1u;
+                        c1 += (uint32_t)__popc(m);
+                    }
+                    emit(B[bs], c1);
+                }
+                for (int q = warp; q < nl; q += LP_NT / 32) {
+                    // larger bins: copies of the first key counted from the
+                    // mask, the other keys compacted into A and counted there
+                    const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
+                    if (len <= (uint32_t)LS_MED) continue;
+                    uint32_t c1 = 0, kept = 0;
+                    for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+                        const uint32_t i = bs + i0 + lane;
+                        const bool in = i < be;
+                        const bool f = in && ((s_eqf[i >> 5] >> (i & 31)) & 1u);
+                        c1 += (uint32_t)__popc(__ballot_sync(0xffffffffu, f));
+                        const bool rest = in && !f;
+                        const uint32_t rm = __ballot_sync(0xffffffffu, rest);
+                        if (rest) A[bs + kept + (uint32_t)__popc(rm & ((1u << lane) - 1u))] = B[i];
+                        kept += (uint32_t)__popc(rm);
+                    }
+                    if (lane == 0) emit(B[bs], c1);
+                    __syncwarp();
+                    if (kept)
+                        warp_bin<Cfg::STACK>(A, B, bs, kept, s2, s1 == 0, 0, s_stack, &s_sp, &s_abort, err, emit);
+                }
+            }
+            __syncthreads();
+            // ---- further 8-bit partitions of large bins that are not all equal
+            for (;;) {
+                const int sp = s_sp;
+                if (sp == 0 || s_abort) break;
+                const LsBin bin = s_stack[sp - 1];
+                __syncthreads();
+                if (tid == 0) {
+                    s_sp = sp - 1;
+                    s_nl = 0;
+                }
+                K* X = bin.buf ? B : A;
+                K* Y = bin.buf ? A : B;
+                s_cnt[tid] = 0;
+                __syncthreads();
+                for (uint32_t i = tid; i < bin.len; i += LP_NT)
+                    atomicAdd(&s_cnt[key_digit(X[bin.beg + i], bin.shift, 0xFF)], 1u);
+                __syncthreads();
+                const uint32_t cnt = s_cnt[tid];
+                uint32_t t2;
+                const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, t2);
+                s_cur[tid] = ex;
+                __syncthreads();
+                for (uint32_t i = tid; i < bin.len; i += LP_NT) {
+                    const K v = X[bin.beg + i];
+                    Y[bin.beg + atomicAdd(&s_cur[key_digit(v, bin.shift, 0xFF)], 1u)] = v;
+                }
+                __syncthreads();
+                const uint32_t sb = bin.beg + ex;
+                if (cnt == 1) emit(Y[sb], 1u);
+                else if (cnt > 1 && cnt <= (uint32_t)LS_SMALL) thread_bin(Y + sb, cnt, emit);
+                else if (cnt > (uint32_t)LS_SMALL)
+                    s_list[atomicAdd(&s_nl, 1)] = sb | (cnt << 16);
+                __syncthreads();
+                const int nl2 = s_nl;
+                for (int q = warp; q < nl2; q += LP_NT / 32)
+                    warp_bin<Cfg::STACK>(Y, X, s_list[q] & 0xFFFFu, s_list[q] >> 16, bin.shift > 8 ? bin.shift - 8 : 0,
+                             bin.shift == 0, bin.buf ^ 1, s_stack, &s_sp, &s_abort, err, emit);
+                __syncthreads();
+            }
+            // s_abort: an impossible bin was met (raise_error has been called)
+            __syncthreads();
+            if (tid == 0) kc[s] = s_kept;
+        }
+    }
+    if (my_ones) atomicAdd(&s_hist[1], my_ones);  // hist_len >= 2: count 1 has its own bin
+    __syncthreads();
+    for (uint32_t i = tid; i < hs; i += LP_NT)
+        if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(hist + i), (unsigned long long)s_hist[i]);
+    // per-CTA totals
+    my_distinct = warp_incl_sum<u64>(my_distinct);
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t v = __shfl_xor_sync(0xffffffffu, my_max, o);
+        my_max = v > my_max ? v : my_max;
+    }
+    if (lane == 31 && my_distinct) atomicAdd(n_distinct, (unsigned long long)my_distinct);
+    if (lane == 0 && my_max) atomicMax(max_count, my_max);
+}
+
+void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, bool big, int shift0,
+                       int key_words, void* keys, uint32_t* kcount, uint32_t* kc, uint32_t* ov_list,
+                       uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
+                       uint32_t* max_count, uint64_t* n_distinct, uint32_t* claim, int* err, int num_sms,
+                       cudaStream_t st) {
+    if (n_sub == 0) return;
+    count_launch();
+    const size_t dyn = local_smem_bytes(key_words, big);
+    auto go = [&](auto kern, auto* kp) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, LP_NT, dyn);
+        if (occ < 1) occ = 1;
+        uint64_t want = ((uint64_t)n_sub + LS_BATCH - 1) / LS_BATCH;
+        uint64_t g = (uint64_t)num_sms * occ;
+        if (want < g) g = want;
+        kern<<<(unsigned)g, LP_NT, dyn, st>>>((const u64*)sub_off, only, n_sub, shift0, kp, kcount, kc, ov_list,
+                                              (unsigned long long*)ov_stats, lo, hi, (u64*)hist, hist_len,
+                                              max_count, (unsigned long long*)n_distinct, claim, err);
+    };
+    if (key_words == 1) {
+        if (big) go(k_local_sort<u64, true>, (u64*)keys);
+        else go(k_local_sort<u64, false>, (u64*)keys);
+    } else {
+        if (big) go(k_local_sort<key128, true>, (key128*)keys);
+        else go(k_local_sort<key128, false>, (key128*)keys);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kept pairs -> output; listed sub-segments -> one array
+// ---------------------------------------------------------------------------
+// Warp w copies the kc[s] kept pairs of sub-segment s (from its range start)
+// to out_keys[out_off[s] ...], for s = w, w + warps, ...
+template <typename K>
+__global__ void __launch_bounds__(256) k_compact(const u64* __restrict__ sub_off, const uint32_t* __restrict__ kc,
+                                                 const u64* __restrict__ out_off, uint32_t n_sub,
+                                                 const K* __restrict__ keys, const uint32_t* __restrict__ kcount,
+                                                 K* __restrict__ out_keys, uint32_t* __restrict__ out_counts,
+                                                 u64 out_cap, int* err) {
+    const int lane = threadIdx.x & 31;
+    const u64 nwarps = (u64)gridDim.x * 8;
+    for (u64 s = (u64)blockIdx.x * 8 + (threadIdx.x >> 5); s < n_sub; s += nwarps) {
+        const uint32_t n = kc[s];
+        if (!n) continue;
+        const u64 src = sub_off[s], dst = out_off[s];
+        if (dst + n > out_cap) {
+            if (lane == 0) raise_error(err, HSK_DERR_BOUNDS);
+            continue;
+        }
+        for (uint32_t i = lane; i < n; i += 32) {
+            out_keys[dst + i] = keys[src + i];
+            out_counts[dst + i] = kcount[src + i];
+        }
+    }
+}
+
+void launch_compact(const uint64_t* sub_off, const uint32_t* kc, const uint64_t* out_off, uint32_t n_sub,
+                    int key_words, const void* keys, const uint32_t* kcount, void* out_keys, uint32_t* out_counts,
+                    uint64_t out_cap, int* err, int grid, cudaStream_t st) {
+    if (n_sub == 0) return;
+    count_launch();
+    uint64_t want = ((uint64_t)n_sub + 7) / 8;
+    unsigned g = (unsigned)(want < (uint64_t)grid ? want : (uint64_t)grid);
+    if (key_words == 1)
+        k_compact<u64><<<g, 256, 0, st>>>((const u64*)sub_off, kc, (const u64*)out_off, n_sub, (const u64*)keys,
+                                          kcount, (u64*)out_keys, out_counts, out_cap, err);
+    else
+        k_compact<key128><<<g, 256, 0, st>>>((const u64*)sub_off, kc, (const u64*)out_off, n_sub,
+                                             (const key128*)keys, kcount, (key128*)out_keys, out_counts, out_cap,
+                                             err);
+}
+
+// One CTA: ov_pre[j] = sum of the sizes of listed sub-segments before j.
+__global__ void __launch_bounds__(256) k_ov_prefix(const u64* __restrict__ sub_off, const uint32_t* __restrict__ ov_list,
+                                                   uint32_t n_ov, u64* __restrict__ ov_pre) {
+    __shared__ u64 s_scr[9];
+    u64 carry = 0;
+    for (uint32_t j0 = 0; j0 < n_ov; j0 += 256) {
+        const uint32_t j = j0 + threadIdx.x;
+        u64 v = 0;
+        if (j < n_ov) {
+            const uint32_t s = ov_list[j];
+            v = sub_off[s + 1] - sub_off[s];
+        }
+        u64 total;
+        const u64 e = block_excl_sum<256, u64>(v, s_scr, total);
+        if (j < n_ov) ov_pre[j] = carry + e;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ov_pre[n_ov] = carry;
+}
+
+// CTA j (stride gridDim.x) copies listed sub-segment j to dst[ov_pre[j] ...].
+template <typename K>
+__global__ void __launch_bounds__(256) k_ov_gather(const u64* __restrict__ sub_off, const uint32_t* __restrict__ ov_list,
+                                                   uint32_t n_ov, const u64* __restrict__ ov_pre,
+                                                   const K* __restrict__ keys, K* __restrict__ dst, u64 dst_cap,
+                                                   int* err) {
+    for (uint32_t j = blockIdx.x; j < n_ov; j += gridDim.x) {
+        const uint32_t s = ov_list[j];
+        const u64 src = sub_off[s], n = sub_off[s + 1] - src, o = ov_pre[j];
+        if (o + n > dst_cap) {
+            if (threadIdx.x == 0) raise_error(err, HSK_DERR_BOUNDS);
+            continue;
+        }
+        for (u64 i = threadIdx.x; i < n; i += 256) dst[o + i] = keys[src + i];
+    }
+}
+
+void launch_ov_gather(const uint64_t* sub_off, const uint32_t* ov_list, uint32_t n_ov, uint64_t* ov_pre,
+                      int key_words, const void* keys, void* dst, uint64_t dst_cap, int* err, int grid,
+                      cudaStream_t st) {
+    if (n_ov == 0) return;
+    count_launch(2);
+    k_ov_prefix<<<1, 256, 0, st>>>((const u64*)sub_off, ov_list, n_ov, (u64*)ov_pre);
+    unsigned g = n_ov < (uint32_t)grid ? n_ov : (unsigned)grid;
+    if (key_words == 1)
+        k_ov_gather<u64><<<g, 256, 0, st>>>((const u64*)sub_off, ov_list, n_ov, (const u64*)ov_pre,
+                                            (const u64*)keys, (u64*)dst, dst_cap, err);
+    else
+        k_ov_gather<key128><<<g, 256, 0, st>>>((const u64*)sub_off, ov_list, n_ov, (const u64*)ov_pre,
+                                               (const key128*)keys, (key128*)dst, dst_cap, err);
+}
+
+}  // namespace hsk

@@ -32,38 +32,9 @@ constexpr int MAX_PASS = 16;
 // ---------------------------------------------------------------------------
 // supermer records -> keys (+ digit histograms), per segment
 // ---------------------------------------------------------------------------
-constexpr int EXP_RPT = 4;                 // records per thread
-constexpr int EXP_TILE = 256 * EXP_RPT;    // records per tile
 
 uint64_t expand_tiles(uint64_t n_rec) { return (n_rec + EXP_TILE - 1) / EXP_TILE; }
 int expand_grid(int num_sms) { return num_sms * 4; }
-
-__device__ __forceinline__ u64 sel4(const u64 (&W)[4], uint32_t i) {
-    return i == 0 ? W[0] : i == 1 ? W[1] : i == 2 ? W[2] : i == 3 ? W[3] : 0ULL;
-}
-
-// k-mer j (k <= 32) of a record held in registers (no local-memory indexing).
-__device__ __forceinline__ u64 record_kmer64(const u64 (&W)[4], uint32_t j, int k) {
-    uint32_t i = j >> 5, off = (j & 31) * 2;
-    return funnel64(sel4(W, i), sel4(W, i + 1), off) >> (64 - 2 * k);
-}
-
-// k-mer j (33 <= k <= 64) of a record held in registers.
-__device__ __forceinline__ key128 record_kmer128(const u64 (&W)[4], uint32_t j, int k) {
-    uint32_t i = j >> 5, off = (j & 31) * 2;
-    u64 a = funnel64(sel4(W, i), sel4(W, i + 1), off);
-    u64 b = funnel64(sel4(W, i + 1), sel4(W, i + 2), off);
-    int s = 128 - 2 * k;
-    key128 r;
-    if (s == 0) {
-        r.hi = a;
-        r.lo = b;
-    } else {
-        r.hi = a >> s;
-        r.lo = (b >> s) | (a << (64 - s));
-    }
-    return r;
-}
 
 // Each CTA starts on segment blockIdx.x % C and takes that segment's record
 // tiles from its counter; when they run out it flushes the segment's

@@ -145,3 +145,45 @@ def test_repeated_calls_reuse_the_arena(hsk, tiny):
     with hsk.Context() as ctx:
         for i in range(25):
             assert_same_result(ctx.count(reads, offs, 31, 17, 2, 50), want, f"call {i}")
+
+
+@pytest.mark.parametrize("case", ["tiny", "one_bucket", "k55", "repeats", "small_hist"])
+def test_on_chip_and_global_paths_agree(hsk, tiny, case):
+    """The on-chip sub-segment sort and the global radix passes give the same
+    bytes; one bucket forces sub-segments over the on-chip capacity, so the
+    fallback path runs next to the on-chip one."""
+    kw = dict(hist_len=65536)
+    k, m, lo, hi = 31, 17, 2, 1000
+    if case == "tiny":
+        reads, offs = tiny.reads, tiny.offsets
+    elif case == "one_bucket":
+        # 2.4 M keys in one bucket: 256 sub-segments of ~9 K keys, the largest
+        # past both on-chip capacities, so all three paths run
+        reads, offs = tiny.reads, tiny.offsets
+        kw["n_buckets"] = 1
+    elif case == "k55":
+        rs = datagen.batched_set(datagen.derive_seed(5, 1), 300_000, 20.0)
+        reads, offs, k, m, lo, hi = rs.reads, rs.offsets, 55, 21, 2, 500
+    elif case == "repeats":
+        # a few sequences repeated thousands of times next to random reads
+        r, o = datagen.random_reads(31, 2000, 50, 300)
+        rep = np.frombuffer(b"ACGTTGCAAGGCTTAACCGGATCGATTACGGCATCAGGACTTGACA" * 3, np.uint8)
+        parts = [r] + [rep] * 3000
+        reads = np.concatenate(parts)
+        lens = np.concatenate([np.diff(o.astype(np.int64)), np.full(3000, rep.size)])
+        offs = np.zeros(lens.size + 1, np.uint64)
+        offs[1:] = np.cumsum(lens)
+        lo, hi = 1, 100000
+    else:
+        n = 4000
+        reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+        kw["hist_len"] = 7
+        lo, hi = 1, 3
+    want = oracle.count(reads, offs, k, lo, hi, hist_len=kw["hist_len"])
+    with hsk.Context(local_sort=True, **kw) as a, hsk.Context(local_sort=False, **kw) as b:
+        ga = a.count(reads, offs, k, m, lo, hi)
+        gb = b.count(reads, offs, k, m, lo, hi)
+        if case == "one_bucket":
+            assert a.last_overflow() > 0  # the global fallback ran next to the on-chip passes
+    assert_same_result(ga, want, f"{case} on-chip")
+    assert_same_result(gb, want, f"{case} global")
