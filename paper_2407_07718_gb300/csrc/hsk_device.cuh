@@ -374,4 +374,72 @@ tile_key(const u64* s_rec, const uint32_t* s_pre, uint32_t nr, uint32_t j, int k
     else return canonical64(record_kmer64(W, jj, k), k);
 }
 
+
+// Calls f(j, key) for the canonical k-mers j = 0 .. n-1 of a supermer record
+// (record words W, bases packed from the most significant bit of W[0]): the
+// first k-mer is cut out of the words, every next one rolls the forward code
+// one base left and the reverse complement one base right.
+template <bool WIDE, typename F>
+__device__ __forceinline__ void record_kmers(const u64 (&W)[4], uint32_t n, int k, F&& f) {
+    if (n == 0) return;
+    const int kk = 2 * k;
+    if constexpr (!WIDE) {
+        const u64 mask = kk == 64 ? ~0ULL : ((1ULL << kk) - 1);
+        u64 fwd = W[0] >> (64 - kk);
+        u64 rc = revcomp64(fwd, k);
+        u64 h, l;  // the bases after the first k-mer, most significant first
+        if (kk == 64) {
+            h = W[1];
+            l = 0;
+        } else {
+            h = (W[0] << kk) | (W[1] >> (64 - kk));
+            l = W[1] << kk;
+        }
+        f(0u, fwd < rc ? fwd : rc);
+        for (uint32_t j = 1; j < n; ++j) {
+            const u64 b = h >> 62;
+            h = (h << 2) | (l >> 62);
+            l <<= 2;
+            fwd = ((fwd << 2) | b) & mask;
+            rc = (rc >> 2) | ((3ULL - b) << (kk - 2));
+            f(j, fwd < rc ? fwd : rc);
+        }
+    } else {
+        const int s = 128 - kk;  // 0 .. 62
+        key128 fwd;
+        if (s == 0) {
+            fwd.hi = W[0];
+            fwd.lo = W[1];
+        } else {
+            fwd.hi = W[0] >> s;
+            fwd.lo = (W[1] >> s) | (W[0] << (64 - s));
+        }
+        key128 rc = revcomp128(fwd, k);
+        const int q = kk - 64;  // 2 .. 64: bits of the codes' high words
+        const u64 himask = q == 64 ? ~0ULL : ((1ULL << q) - 1);
+        u64 h, m, l;
+        if (q == 64) {
+            h = W[2];
+            m = W[3];
+            l = 0;
+        } else {
+            h = (W[1] << q) | (W[2] >> (64 - q));
+            m = (W[2] << q) | (W[3] >> (64 - q));
+            l = W[3] << q;
+        }
+        f(0u, key_lt(fwd, rc) ? fwd : rc);
+        for (uint32_t j = 1; j < n; ++j) {
+            const u64 b = h >> 62;
+            h = (h << 2) | (m >> 62);
+            m = (m << 2) | (l >> 62);
+            l <<= 2;
+            fwd.hi = ((fwd.hi << 2) | (fwd.lo >> 62)) & himask;
+            fwd.lo = (fwd.lo << 2) | b;
+            rc.lo = (rc.lo >> 2) | (rc.hi << 62);
+            rc.hi = (rc.hi >> 2) | ((3ULL - b) << (q - 2));
+            f(j, key_lt(fwd, rc) ? fwd : rc);
+        }
+    }
+}
+
 }  // namespace hsk

@@ -41,23 +41,25 @@ constexpr int LP_NT = 256;
 template <bool WIDE>
 struct PartCfg {
     static constexpr int ROUND = WIDE ? 2048 : 4096;  // keys grouped per scatter round
-    static constexpr int IPT = ROUND / LP_NT;
 };
 
 size_t part_smem_bytes(int mode, int k) {
-    const bool wide = k > 32;
-    const size_t rec = (size_t)EXP_TILE * (wide ? 4 : 2) * 8;
-    if (mode == 0) return rec;
-    return rec + (size_t)(wide ? PartCfg<true>::ROUND * 16 : PartCfg<false>::ROUND * 8);
+    if (mode == 0) return 0;
+    return 2 * (k > 32 ? (size_t)PartCfg<true>::ROUND * 16 : (size_t)PartCfg<false>::ROUND * 8);
 }
 
 // Work: one counter over all record tiles of all groups; tile g belongs to
-// group tile_seg[g] and is tile g - tile_base[group] of it.
+// group tile_seg[g] and is tile g - tile_base[group] of it.  Thread t holds
+// records t, t + 256, ... of the tile (EXP_RPT of them) and rolls through
+// their k-mers (record_kmers).
 // MODE 0: sub_cnt[c * 256 + d] += keys of group c whose digit at `shift` is d.
 // MODE 1: every key to keys_out[cursor[c * 256 + d]++] (a reservation per
-//         digit and round), never past sub_end[c * 256 + d].
+//         digit and round), never past sub_end[c * 256 + d].  A round takes
+//         the tile's keys [j0, j0 + ROUND) in record order: the records that
+//         reach into the window write their keys there, the round is grouped
+//         by digit in shared memory and written out as one run per digit.
 template <bool WIDE, int MODE>
-__global__ void __launch_bounds__(LP_NT) k_part(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
+__global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
                                                 const u64* __restrict__ tile_base, const uint32_t* __restrict__ tile_seg,
                                                 uint32_t n_tiles, int k, int shift, uint32_t* tile_ctr,
                                                 uint32_t* __restrict__ sub_cnt, unsigned long long* cursor,
@@ -65,18 +67,16 @@ __global__ void __launch_bounds__(LP_NT) k_part(const u64* __restrict__ rec, con
                                                 int* err) {
     using K = typename std::conditional<WIDE, key128, u64>::type;
     constexpr int RW = WIDE ? 4 : 2;
-    constexpr int ROUND = PartCfg<WIDE>::ROUND, IPT = PartCfg<WIDE>::IPT;
+    constexpr int ROUND = PartCfg<WIDE>::ROUND;
     extern __shared__ __align__(16) u64 smem_part[];
-    u64* s_rec = smem_part;                                         // EXP_TILE * RW words
-    K* s_keys = reinterpret_cast<K*>(smem_part + EXP_TILE * RW);    // ROUND keys (MODE 1)
-    __shared__ uint32_t s_pre[EXP_TILE + 1];
+    K* s_raw = reinterpret_cast<K*>(smem_part);  // a round's keys in tile order (MODE 1)
+    K* s_keys = s_raw + ROUND;                    // the same keys grouped by digit
     __shared__ uint32_t s_cnt[256], s_fill[256], s_dstart[256];
     __shared__ u64 s_gbase[256];
-    __shared__ u64 s_scr[9];
     __shared__ uint32_t s_scr32[9];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x;
-    if (MODE == 0) s_cnt[tid] = 0;
+    s_cnt[tid] = 0;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
@@ -88,86 +88,99 @@ __global__ void __launch_bounds__(LP_NT) k_part(const u64* __restrict__ rec, con
         const u64 rb = rec_base[c], n_rec = rec_base[c + 1] - rb;
         const u64 r0 = tile * EXP_TILE;
         const uint32_t nr = (uint32_t)(n_rec - r0 < (u64)EXP_TILE ? n_rec - r0 : (u64)EXP_TILE);
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rec + (rb + r0) * RW);
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rec);
-        for (uint32_t i = tid; i < nr * (RW / 2); i += LP_NT) dst[i] = src[i];
-        __syncthreads();
-        uint32_t nk[EXP_RPT], sum = 0;
+        const u64* trec = rec + (rb + r0) * RW;
+        // this thread's records, in registers
+        u64 W[EXP_RPT][4];
+        uint32_t nk[EXP_RPT];
 #pragma unroll
         for (int i = 0; i < EXP_RPT; ++i) {
-            const uint32_t r = tid * EXP_RPT + i;
-            nk[i] = r < nr ? (uint32_t)(s_rec[r * RW + RW - 1] & 0xFF) : 0u;
-            sum += nk[i];
-        }
-        u64 total;
-        const u64 excl = block_excl_sum<LP_NT, u64>((u64)sum, s_scr, total);
-        {
-            uint32_t run = (uint32_t)excl;
-#pragma unroll
-            for (int i = 0; i < EXP_RPT; ++i) {
-                s_pre[tid * EXP_RPT + i] = run;
-                run += nk[i];
+            const uint32_t r = (uint32_t)i * LP_NT + tid;
+            nk[i] = 0;
+            W[i][0] = W[i][1] = W[i][2] = W[i][3] = 0;
+            if (r < nr) {
+                const ulonglong2* q = reinterpret_cast<const ulonglong2*>(trec + (u64)r * RW);
+                const ulonglong2 a = q[0];
+                W[i][0] = a.x;
+                W[i][1] = a.y;
+                if (WIDE) {
+                    const ulonglong2 b2 = q[1];
+                    W[i][2] = b2.x;
+                    W[i][3] = b2.y;
+                }
+                nk[i] = (uint32_t)(W[i][RW - 1] & 0xFF);
             }
-            if (tid == LP_NT - 1) s_pre[EXP_TILE] = run;
         }
-        __syncthreads();
-        const uint32_t T = (uint32_t)total;
         if (MODE == 0) {
-            for (uint32_t j = tid; j < T; j += LP_NT) {
-                const K key = tile_key<WIDE>(s_rec, s_pre, nr, j, k);
-                atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u);
-            }
+#pragma unroll
+            for (int i = 0; i < EXP_RPT; ++i)
+                record_kmers<WIDE>(W[i], nk[i], k,
+                                   [&](uint32_t, const K& key) { atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u); });
             __syncthreads();
             const uint32_t v = s_cnt[tid];
             if (v) atomicAdd(sub_cnt + (u64)c * 256 + tid, v);
             s_cnt[tid] = 0;
-        } else {
-            K* out = reinterpret_cast<K*>(keys_out);
-            for (uint32_t j0 = 0; j0 < T; j0 += ROUND) {
-                const uint32_t nround = T - j0 < (uint32_t)ROUND ? T - j0 : (uint32_t)ROUND;
-                s_cnt[tid] = 0;
-                __syncthreads();
-                K kk[IPT];
-                uint32_t dd[IPT];
+            continue;
+        }
+        // record r's keys are tile keys [pre[i], pre[i] + nk[i]); records are
+        // taken in the order i * 256 + tid, so the prefix runs over (i, tid)
+        uint32_t pre[EXP_RPT];
+        uint32_t T = 0;
+        {
+            uint32_t run = 0;
 #pragma unroll
-                for (int i = 0; i < IPT; ++i) {
-                    const uint32_t j = (uint32_t)i * LP_NT + tid;
-                    if (j < nround) {
-                        kk[i] = tile_key<WIDE>(s_rec, s_pre, nr, j0 + j, k);
-                        dd[i] = key_digit(kk[i], shift, 0xFF);
-                        atomicAdd(&s_cnt[dd[i]], 1u);
-                    }
-                }
-                __syncthreads();
-                const uint32_t cnt = s_cnt[tid];
+            for (int i = 0; i < EXP_RPT; ++i) {
                 uint32_t tot;
-                const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, tot);
-                s_dstart[tid] = ex;
-                s_fill[tid] = ex;
-                if (cnt) {
-                    const u64 slot = (u64)c * 256 + tid;
-                    u64 at = atomicAdd(cursor + slot, (unsigned long long)cnt);
-                    if (at + cnt > sub_end[slot]) {
-                        raise_error(err, HSK_DERR_BOUNDS);
-                        at = ~0ULL;
-                    }
-                    s_gbase[tid] = at;
-                }
-                __syncthreads();
-#pragma unroll
-                for (int i = 0; i < IPT; ++i) {
-                    const uint32_t j = (uint32_t)i * LP_NT + tid;
-                    if (j < nround) s_keys[atomicAdd(&s_fill[dd[i]], 1u)] = kk[i];
-                }
-                __syncthreads();
-                for (uint32_t i = tid; i < nround; i += LP_NT) {
-                    const K key = s_keys[i];
-                    const uint32_t d = key_digit(key, shift, 0xFF);
-                    const u64 at = s_gbase[d];
-                    if (at != ~0ULL) out[at + (i - s_dstart[d])] = key;
-                }
-                __syncthreads();
+                const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(nk[i], s_scr32, tot);
+                pre[i] = run + ex;
+                run += tot;
             }
+            T = run;
+        }
+        K* out = reinterpret_cast<K*>(keys_out);
+        for (uint32_t j0 = 0; j0 < T; j0 += ROUND) {
+            const uint32_t nround = T - j0 < (uint32_t)ROUND ? T - j0 : (uint32_t)ROUND;
+            s_cnt[tid] = 0;
+            __syncthreads();
+            // keys of this round into s_keys (tile order), digits counted
+#pragma unroll
+            for (int i = 0; i < EXP_RPT; ++i) {
+                if (pre[i] + nk[i] > j0 && pre[i] < j0 + nround)
+                    record_kmers<WIDE>(W[i], nk[i], k, [&](uint32_t j, const K& key) {
+                        const uint32_t pos = pre[i] + j;
+                        if (pos >= j0 && pos < j0 + nround) {
+                            s_raw[pos - j0] = key;
+                            atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u);
+                        }
+                    });
+            }
+            __syncthreads();
+            const uint32_t cnt = s_cnt[tid];
+            uint32_t tot;
+            const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, tot);
+            s_dstart[tid] = ex;
+            s_fill[tid] = ex;
+            if (cnt) {
+                const u64 slot = (u64)c * 256 + tid;
+                u64 at = atomicAdd(cursor + slot, (unsigned long long)cnt);
+                if (at + cnt > sub_end[slot]) {
+                    raise_error(err, HSK_DERR_BOUNDS);
+                    at = ~0ULL;
+                }
+                s_gbase[tid] = at;
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < nround; j += LP_NT) {  // group the round by digit
+                const K key = s_raw[j];
+                s_keys[atomicAdd(&s_fill[key_digit(key, shift, 0xFF)], 1u)] = key;
+            }
+            __syncthreads();
+            for (uint32_t i = tid; i < nround; i += LP_NT) {
+                const K key = s_keys[i];
+                const uint32_t d = key_digit(key, shift, 0xFF);
+                const u64 at = s_gbase[d];
+                if (at != ~0ULL) out[at + (i - s_dstart[d])] = key;
+            }
+            __syncthreads();
         }
     }
 }
