@@ -240,7 +240,6 @@ constexpr int LS_SMALL = 16;       // bins of at most this many keys: counted ke
 constexpr int LS_MED = 256;        // bins of at most this many keys: rank sort by one warp
 constexpr int LS_PEEL = 8;         // distinct keys peeled off a bin before it is sorted
 constexpr int LS_HS = 128;         // count-histogram bins kept in shared memory
-constexpr int LS_BATCH = 2;        // sub-segments claimed at once
 // open bins are disjoint and hold > LS_MED keys; listed bins hold > LS_SMALL
 #define HSK_LS_CHECK(K, BIG)                                                                        \
     static_assert(LocalCfg<K, BIG>::CAP / (LS_MED + 1) < LocalCfg<K, BIG>::STACK, "stack too small"); \
@@ -378,6 +377,23 @@ __device__ __forceinline__ void warp_bin(K* src, K* other, uint32_t sb, uint32_t
     }
 }
 
+// Keys of sub-segment (list entry) idx into pf: thread t takes keys t,
+// t + 256, ...; nothing when idx is past the end or the sub-segment is too
+// large for one CTA.
+template <int CAP, typename K, int PFN>
+__device__ __forceinline__ void ls_prefetch(K (&pf)[PFN], const K* keys, const u64* sub_off, const uint32_t* only,
+                                            uint32_t n_sub, uint32_t idx) {
+    if (idx >= n_sub) return;
+    const uint32_t ps = only ? only[idx] : idx;
+    const u64 pb = sub_off[ps], pm = sub_off[ps + 1] - pb;
+    if (pm > (u64)CAP) return;
+#pragma unroll
+    for (int j = 0; j < PFN; ++j) {
+        const uint32_t i = (uint32_t)j * LP_NT + threadIdx.x;
+        if (i < pm) pf[j] = keys[pb + i];
+    }
+}
+
 // Sub-segment s holds keys [sub_off[s], sub_off[s+1]) of `keys`; its top
 // digit (bits shift0 and up) is common to all of them.  The first partition
 // takes the next LS_D1 bits (count while loading, scan, scatter A -> B), so
@@ -387,7 +403,7 @@ __device__ __forceinline__ void warp_bin(K* src, K* other, uint32_t sb, uint32_t
 // (in no particular order: stage S6 orders all pairs).  The counts of all
 // runs go to the histogram, their number to n_distinct, the largest to max_count.
 template <typename K, bool BIG>
-__global__ void __launch_bounds__(LP_NT) k_local_sort(const u64* __restrict__ sub_off,
+__global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __restrict__ sub_off,
                                                       const uint32_t* __restrict__ only, uint32_t n_sub, int shift0,
                                                       K* keys, uint32_t* __restrict__ kcount,
                                                       uint32_t* __restrict__ kc, uint32_t* __restrict__ ov_list,
@@ -411,7 +427,7 @@ __global__ void __launch_bounds__(LP_NT) k_local_sort(const u64* __restrict__ su
     __shared__ LsBin s_stack[Cfg::STACK];
     __shared__ uint32_t s_scr32[9];
     __shared__ int s_sp, s_abort, s_nl;
-    __shared__ uint32_t s_kept, s_batch;
+    __shared__ uint32_t s_kept, s_next;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t hs = hist_len < (uint32_t)LS_HS ? hist_len : (uint32_t)LS_HS;
     const int s1 = shift0 > LS_D1 ? shift0 - LS_D1 : 0;  // first partition's digit
@@ -457,196 +473,199 @@ __global__ void __launch_bounds__(LP_NT) k_local_sort(const u64* __restrict__ su
             }
         }
     };
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_batch = atomicAdd(claim, (uint32_t)LS_BATCH);
-        __syncthreads();
-        const uint32_t b0 = s_batch;
-        if (b0 >= n_sub) break;
-        const uint32_t b1 = b0 + LS_BATCH < n_sub ? b0 + LS_BATCH : n_sub;
-        for (uint32_t si = b0; si < b1; ++si) {
-            const uint32_t s = only ? only[si] : si;
-            base = sub_off[s];
-            const u64 n64 = sub_off[s + 1] - base;
-            if (n64 == 0) {
-                if (tid == 0) kc[s] = 0;
-                continue;
-            }
-            if (n64 > (u64)CAP) {
-                if (tid == 0) {
-                    kc[s] = 0;
+    // Sub-segments are claimed one at a time; the next one's keys are loaded
+    // into registers while the current one is sorted (first pass only).
+    constexpr int PF = BIG ? 0 : CAP / LP_NT;
+    constexpr int PFN = PF > 0 ? PF : 1;
+    K pf[PFN];
+    if (tid == 0) s_next = atomicAdd(claim, 1u);
+    __syncthreads();
+    uint32_t si = s_next;
+    if (PF) ls_prefetch<CAP>(pf, keys, sub_off, only, n_sub, si);
+    while (si < n_sub) {
+        const uint32_t s = only ? only[si] : si;
+        base = sub_off[s];
+        const u64 n64 = sub_off[s + 1] - base;
+        __syncthreads();  // every thread has read s_next; the last sub-segment's shared state is free
+        if (tid == 0) s_next = atomicAdd(claim, 1u);
+        if (n64 == 0 || n64 > (u64)CAP) {
+            if (tid == 0) {
+                kc[s] = 0;
+                if (n64) {
                     ov_list[atomicAdd(reinterpret_cast<unsigned int*>(ov_stats), 1u)] = s;
                     atomicAdd(ov_stats + 1, (unsigned long long)n64);
                 }
-                continue;
             }
-            const uint32_t n = (uint32_t)n64;
-            if (tid == 0) {
-                s_sp = 0;
-                s_abort = 0;
-                s_kept = 0;
-                s_nl = 0;
-            }
-            if (shift0 == 0) {  // the top digit is the whole key: one run
-                __syncthreads();
-                if (tid == 0) emit(keys[base], n);
-                __syncthreads();
-                if (tid == 0) kc[s] = s_kept;
-                continue;
-            }
-            // ---- first partition: load + count, scan, scatter A -> B
-#pragma unroll
-            for (int j = 0; j < 8; ++j) s_cnt1[tid * 8 + j] = 0;
             __syncthreads();
+            si = s_next;
+            if (PF) ls_prefetch<CAP>(pf, keys, sub_off, only, n_sub, si);
+            continue;
+        }
+        const uint32_t n = (uint32_t)n64;
+        if (tid == 0) {
+            s_sp = 0;
+            s_abort = 0;
+            s_kept = 0;
+            s_nl = 0;
+        }
+        if (shift0 == 0) {  // the top digit is the whole key: one run
+            __syncthreads();
+            if (tid == 0) {
+                emit(keys[base], n);
+                kc[s] = s_kept;
+            }
+            si = s_next;
+            if (PF) ls_prefetch<CAP>(pf, keys, sub_off, only, n_sub, si);
+            continue;
+        }
+        // ---- first partition: load + count, scan, scatter A -> B
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s_cnt1[tid * 8 + j] = 0;
+        __syncthreads();
+        if (PF > 0) {
+#pragma unroll
+            for (int j = 0; j < PFN; ++j) {
+                const uint32_t i = (uint32_t)j * LP_NT + tid;
+                if (i < n) {
+                    A[i] = pf[j];
+                    atomicAdd(&s_cnt1[key_digit(pf[j], s1, LS_B1 - 1)], 1u);
+                }
+            }
+        } else {
             for (uint32_t i = tid; i < n; i += LP_NT) {
                 const K v = keys[base + i];
                 A[i] = v;
                 atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u);
             }
-            __syncthreads();
-            uint32_t bc[8], sum = 0;
+        }
+        __syncthreads();
+        const uint32_t nxt = s_next;
+        if (PF) ls_prefetch<CAP>(pf, keys, sub_off, only, n_sub, nxt);
+        uint32_t bc[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            bc[j] = s_cnt1[tid * 8 + j];
+            sum += bc[j];
+        }
+        uint32_t tot;
+        const uint32_t my0 = block_excl_sum<LP_NT, uint32_t>(sum, s_scr32, tot);
+        {
+            uint32_t run = my0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                bc[j] = s_cnt1[tid * 8 + j];
-                sum += bc[j];
+                s_cnt1[tid * 8 + j] = run;
+                run += bc[j];
             }
-            uint32_t tot;
-            const uint32_t my0 = block_excl_sum<LP_NT, uint32_t>(sum, s_scr32, tot);
-            {
-                uint32_t run = my0;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    s_cnt1[tid * 8 + j] = run;
-                    run += bc[j];
-                }
-            }
-            __syncthreads();
-            for (uint32_t i = tid; i < n; i += LP_NT) {
-                const K v = A[i];
-                B[atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u)] = v;
-            }
-            __syncthreads();
-            // ---- every key: its bin is [end of bin d-1, end of bin d); in a
-            // small bin, count the equal keys and emit at the first of them;
-            // the first key of a larger bin lists the bin for the warps
-            for (uint32_t i0 = 0; i0 < n; i0 += LP_NT) {
-                const uint32_t i = i0 + tid;
-                bool head = false, eqf = false;
-                uint32_t cnt = 0;
-                K v{};
-                if (i < n) {
-                    v = B[i];
-                    const uint32_t d = key_digit(v, s1, LS_B1 - 1);
-                    const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
-                    if (be - bs <= (uint32_t)LS_SMALL) {
-                        head = true;
-                        for (uint32_t j = bs; j < be; ++j)
-                            if (key_eq(B[j], v)) {
-                                ++cnt;
-                                head = head && j >= i;
-                            }
-                    } else {
-                        // larger bin: copies of its first key only mark the mask
-                        // (counted below); in bins of <= LS_MED keys every other
-                        // key counts its equals here, like a small bin's keys
-                        eqf = key_eq(v, B[bs]);
-                        if (!eqf && be - bs <= (uint32_t)LS_MED) {
-                            head = true;
-                            for (uint32_t j = bs; j < be; ++j)
-                                if (key_eq(B[j], v)) {
-                                    ++cnt;
-                                    head = head && j >= i;
-                                }
-                        }
-                        if (i == bs) s_list[atomicAdd(&s_nl, 1)] = bs | ((be - bs) << 16);
-                    }
-                }
-                const uint32_t fm = __ballot_sync(0xffffffffu, eqf);
-                if (lane == 0 && i0 + (uint32_t)warp * 32 < n) s_eqf[(i0 >> 5) + warp] = fm;
-                emit_warp(head, v, cnt);
-            }
-            __syncthreads();
-            {
-                const int nl = s_nl;
-                // bins of <= LS_MED keys: the first key's count is a popcount of the mask
-                for (int q = tid; q < nl; q += LP_NT) {
-                    const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
-                    if (len > (uint32_t)LS_MED) continue;
-                    uint32_t c1 = 0;
-                    for (uint32_t w = bs >> 5; w <= (be - 1) >> 5; ++w) {
-                        uint32_t m = s_eqf[w];
-                        if (w == bs >> 5) m &= 0xFFFFFFFFu << (bs & 31);
-                        if (w == (be - 1) >> 5 && ((be - 1) & 31) != 31) m &= (2u << ((be - 1) & 31)) - 1u;
-                        c1 += (uint32_t)__popc(m);
-                    }
-                    emit(B[bs], c1);
-                }
-                for (int q = warp; q < nl; q += LP_NT / 32) {
-                    // larger bins: copies of the first key counted from the
-                    // mask, the other keys compacted into A and counted there
-                    const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
-                    if (len <= (uint32_t)LS_MED) continue;
-                    uint32_t c1 = 0, kept = 0;
-                    for (uint32_t i0 = 0; i0 < len; i0 += 32) {
-                        const uint32_t i = bs + i0 + lane;
-                        const bool in = i < be;
-                        const bool f = in && ((s_eqf[i >> 5] >> (i & 31)) & 1u);
-                        c1 += (uint32_t)__popc(__ballot_sync(0xffffffffu, f));
-                        const bool rest = in && !f;
-                        const uint32_t rm = __ballot_sync(0xffffffffu, rest);
-                        if (rest) A[bs + kept + (uint32_t)__popc(rm & ((1u << lane) - 1u))] = B[i];
-                        kept += (uint32_t)__popc(rm);
-                    }
-                    if (lane == 0) emit(B[bs], c1);
-                    __syncwarp();
-                    if (kept)
-                        warp_bin<Cfg::STACK>(A, B, bs, kept, s2, s1 == 0, 0, s_stack, &s_sp, &s_abort, err, emit);
-                }
-            }
-            __syncthreads();
-            // ---- further 8-bit partitions of large bins that are not all equal
-            for (;;) {
-                const int sp = s_sp;
-                if (sp == 0 || s_abort) break;
-                const LsBin bin = s_stack[sp - 1];
-                __syncthreads();
-                if (tid == 0) {
-                    s_sp = sp - 1;
-                    s_nl = 0;
-                }
-                K* X = bin.buf ? B : A;
-                K* Y = bin.buf ? A : B;
-                s_cnt[tid] = 0;
-                __syncthreads();
-                for (uint32_t i = tid; i < bin.len; i += LP_NT)
-                    atomicAdd(&s_cnt[key_digit(X[bin.beg + i], bin.shift, 0xFF)], 1u);
-                __syncthreads();
-                const uint32_t cnt = s_cnt[tid];
-                uint32_t t2;
-                const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, t2);
-                s_cur[tid] = ex;
-                __syncthreads();
-                for (uint32_t i = tid; i < bin.len; i += LP_NT) {
-                    const K v = X[bin.beg + i];
-                    Y[bin.beg + atomicAdd(&s_cur[key_digit(v, bin.shift, 0xFF)], 1u)] = v;
-                }
-                __syncthreads();
-                const uint32_t sb = bin.beg + ex;
-                if (cnt == 1) emit(Y[sb], 1u);
-                else if (cnt > 1 && cnt <= (uint32_t)LS_SMALL) thread_bin(Y + sb, cnt, emit);
-                else if (cnt > (uint32_t)LS_SMALL)
-                    s_list[atomicAdd(&s_nl, 1)] = sb | (cnt << 16);
-                __syncthreads();
-                const int nl2 = s_nl;
-                for (int q = warp; q < nl2; q += LP_NT / 32)
-                    warp_bin<Cfg::STACK>(Y, X, s_list[q] & 0xFFFFu, s_list[q] >> 16, bin.shift > 8 ? bin.shift - 8 : 0,
-                             bin.shift == 0, bin.buf ^ 1, s_stack, &s_sp, &s_abort, err, emit);
-                __syncthreads();
-            }
-            // s_abort: an impossible bin was met (raise_error has been called)
-            __syncthreads();
-            if (tid == 0) kc[s] = s_kept;
         }
+        __syncthreads();
+        for (uint32_t i = tid; i < n; i += LP_NT) {
+            const K v = A[i];
+            B[atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u)] = v;
+        }
+        __syncthreads();
+        // ---- every key: its bin is [end of bin d-1, end of bin d).  In a
+        // small bin the key counts its equals and emits at the first of them;
+        // in a larger bin it only marks whether it equals the bin's first key,
+        // and the bin's first key lists the bin
+        for (uint32_t i0 = 0; i0 < n; i0 += LP_NT) {
+            const uint32_t i = i0 + tid;
+            bool head = false, eqf = false;
+            uint32_t cnt = 0;
+            K v{};
+            if (i < n) {
+                v = B[i];
+                const uint32_t d = key_digit(v, s1, LS_B1 - 1);
+                const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
+                if (be - bs <= (uint32_t)LS_SMALL) {
+                    head = true;
+                    for (uint32_t j = bs; j < be; ++j)
+                        if (key_eq(B[j], v)) {
+                            ++cnt;
+                            head = head && j >= i;
+                        }
+                } else {
+                    eqf = key_eq(v, B[bs]);
+                    if (i == bs) s_list[atomicAdd(&s_nl, 1)] = bs | ((be - bs) << 16);
+                }
+            }
+            const uint32_t fm = __ballot_sync(0xffffffffu, eqf);
+            if (lane == 0 && i0 + (uint32_t)warp * 32 < n) s_eqf[(i0 >> 5) + warp] = fm;
+            emit_warp(head, v, cnt);
+        }
+        __syncthreads();
+        {
+            const int nl = s_nl;
+            // one warp per larger bin: the first key's count is a popcount of
+            // the mask, the other keys are compacted into A and counted there
+            for (int q = warp; q < nl; q += LP_NT / 32) {
+                const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
+                const uint32_t w0 = bs >> 5, w1 = (be - 1) >> 5;
+                uint32_t c1 = 0;
+                for (uint32_t w = w0 + lane; w <= w1; w += 32) {
+                    uint32_t m = s_eqf[w];
+                    if (w == w0) m &= 0xFFFFFFFFu << (bs & 31);
+                    if (w == w1 && ((be - 1) & 31) != 31) m &= (2u << ((be - 1) & 31)) - 1u;
+                    c1 += (uint32_t)__popc(m);
+                }
+                for (int o = 16; o > 0; o >>= 1) c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+                if (lane == 0) emit(B[bs], c1);
+                if (c1 == len) continue;
+                uint32_t kept = 0;
+                for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+                    const uint32_t i = bs + i0 + lane;
+                    const bool rest = i < be && !((s_eqf[i >> 5] >> (i & 31)) & 1u);
+                    const uint32_t rm = __ballot_sync(0xffffffffu, rest);
+                    if (rest) A[bs + kept + (uint32_t)__popc(rm & ((1u << lane) - 1u))] = B[i];
+                    kept += (uint32_t)__popc(rm);
+                }
+                __syncwarp();
+                warp_bin<Cfg::STACK>(A, B, bs, kept, s2, s1 == 0, 0, s_stack, &s_sp, &s_abort, err, emit);
+            }
+        }
+        __syncthreads();
+        // ---- further 8-bit partitions of large bins that are not all equal
+        for (;;) {
+            const int sp = s_sp;
+            if (sp == 0 || s_abort) break;
+            const LsBin bin = s_stack[sp - 1];
+            __syncthreads();
+            if (tid == 0) {
+                s_sp = sp - 1;
+                s_nl = 0;
+            }
+            K* X = bin.buf ? B : A;
+            K* Y = bin.buf ? A : B;
+            s_cnt[tid] = 0;
+            __syncthreads();
+            for (uint32_t i = tid; i < bin.len; i += LP_NT)
+                atomicAdd(&s_cnt[key_digit(X[bin.beg + i], bin.shift, 0xFF)], 1u);
+            __syncthreads();
+            const uint32_t cnt = s_cnt[tid];
+            uint32_t t2;
+            const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, t2);
+            s_cur[tid] = ex;
+            __syncthreads();
+            for (uint32_t i = tid; i < bin.len; i += LP_NT) {
+                const K v = X[bin.beg + i];
+                Y[bin.beg + atomicAdd(&s_cur[key_digit(v, bin.shift, 0xFF)], 1u)] = v;
+            }
+            __syncthreads();
+            const uint32_t sb = bin.beg + ex;
+            if (cnt == 1) emit(Y[sb], 1u);
+            else if (cnt > 1 && cnt <= (uint32_t)LS_SMALL) thread_bin(Y + sb, cnt, emit);
+            else if (cnt > (uint32_t)LS_SMALL)
+                s_list[atomicAdd(&s_nl, 1)] = sb | (cnt << 16);
+            __syncthreads();
+            const int nl2 = s_nl;
+            for (int q = warp; q < nl2; q += LP_NT / 32)
+                warp_bin<Cfg::STACK>(Y, X, s_list[q] & 0xFFFFu, s_list[q] >> 16, bin.shift > 8 ? bin.shift - 8 : 0,
+                                     bin.shift == 0, bin.buf ^ 1, s_stack, &s_sp, &s_abort, err, emit);
+            __syncthreads();
+        }
+        // s_abort: an impossible bin was met (raise_error has been called)
+        __syncthreads();
+        if (tid == 0) kc[s] = s_kept;
+        si = nxt;
     }
     if (my_ones) atomicAdd(&s_hist[1], my_ones);  // hist_len >= 2: count 1 has its own bin
     __syncthreads();
@@ -675,7 +694,7 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, LP_NT, dyn);
         if (occ < 1) occ = 1;
-        uint64_t want = ((uint64_t)n_sub + LS_BATCH - 1) / LS_BATCH;
+        uint64_t want = n_sub;
         uint64_t g = (uint64_t)num_sms * occ;
         if (want < g) g = want;
         kern<<<(unsigned)g, LP_NT, dyn, st>>>((const u64*)sub_off, only, n_sub, shift0, kp, kcount, kc, ov_list,
