@@ -403,7 +403,7 @@ __device__ __forceinline__ void ls_prefetch(K (&pf)[PFN], const K* keys, const u
 // (in no particular order: stage S6 orders all pairs).  The counts of all
 // runs go to the histogram, their number to n_distinct, the largest to max_count.
 template <typename K, bool BIG>
-__global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __restrict__ sub_off,
+__global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(const u64* __restrict__ sub_off,
                                                       const uint32_t* __restrict__ only, uint32_t n_sub, int shift0,
                                                       K* keys, uint32_t* __restrict__ kcount,
                                                       uint32_t* __restrict__ kc, uint32_t* __restrict__ ov_list,
@@ -413,6 +413,8 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
                                                       uint32_t* claim, int* err) {
     using Cfg = LocalCfg<K, BIG>;
     constexpr int CAP = Cfg::CAP;
+    constexpr int NT = BIG ? 512 : 256;   // threads
+    constexpr int BPT = LS_B1 / NT;       // first-partition bins per thread
     extern __shared__ __align__(16) unsigned char smem_local[];
     K* A = reinterpret_cast<K*>(smem_local);
     K* B = A + CAP;
@@ -425,14 +427,14 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
     __shared__ uint32_t s_eqf[CAP / 32];   // key equals the first key of its (larger) bin
     __shared__ uint32_t s_hist[LS_HS];
     __shared__ LsBin s_stack[Cfg::STACK];
-    __shared__ uint32_t s_scr32[9];
+    __shared__ uint32_t s_scr32[NT / 32 + 1];
     __shared__ int s_sp, s_abort, s_nl;
     __shared__ uint32_t s_kept, s_next;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t hs = hist_len < (uint32_t)LS_HS ? hist_len : (uint32_t)LS_HS;
     const int s1 = shift0 > LS_D1 ? shift0 - LS_D1 : 0;  // first partition's digit
     const int s2 = s1 > 8 ? s1 - 8 : 0;                 // then 8-bit digits
-    for (int i = tid; i < LS_HS; i += LP_NT) s_hist[i] = 0;
+    for (int i = tid; i < LS_HS; i += NT) s_hist[i] = 0;
     u64 my_distinct = 0;
     uint32_t my_max = 0, my_ones = 0;
     u64 base = 0;
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
     };
     // Sub-segments are claimed one at a time; the next one's keys are loaded
     // into registers while the current one is sorted (first pass only).
-    constexpr int PF = BIG ? 0 : CAP / LP_NT;
+    constexpr int PF = BIG ? 0 : CAP / NT;
     constexpr int PFN = PF > 0 ? PF : 1;
     K pf[PFN];
     if (tid == 0) s_next = atomicAdd(claim, 1u);
@@ -520,19 +522,19 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
         }
         // ---- first partition: load + count, scan, scatter A -> B
 #pragma unroll
-        for (int j = 0; j < 8; ++j) s_cnt1[tid * 8 + j] = 0;
+        for (int j = 0; j < BPT; ++j) s_cnt1[tid * BPT + j] = 0;
         __syncthreads();
         if (PF > 0) {
 #pragma unroll
             for (int j = 0; j < PFN; ++j) {
-                const uint32_t i = (uint32_t)j * LP_NT + tid;
+                const uint32_t i = (uint32_t)j * NT + tid;
                 if (i < n) {
                     A[i] = pf[j];
                     atomicAdd(&s_cnt1[key_digit(pf[j], s1, LS_B1 - 1)], 1u);
                 }
             }
         } else {
-            for (uint32_t i = tid; i < n; i += LP_NT) {
+            for (uint32_t i = tid; i < n; i += NT) {
                 const K v = keys[base + i];
                 A[i] = v;
                 atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u);
@@ -541,24 +543,24 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
         __syncthreads();
         const uint32_t nxt = s_next;
         if (PF) ls_prefetch<CAP>(pf, keys, sub_off, only, n_sub, nxt);
-        uint32_t bc[8], sum = 0;
+        uint32_t bc[BPT], sum = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            bc[j] = s_cnt1[tid * 8 + j];
+        for (int j = 0; j < BPT; ++j) {
+            bc[j] = s_cnt1[tid * BPT + j];
             sum += bc[j];
         }
         uint32_t tot;
-        const uint32_t my0 = block_excl_sum<LP_NT, uint32_t>(sum, s_scr32, tot);
+        const uint32_t my0 = block_excl_sum<NT, uint32_t>(sum, s_scr32, tot);
         {
             uint32_t run = my0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                s_cnt1[tid * 8 + j] = run;
+            for (int j = 0; j < BPT; ++j) {
+                s_cnt1[tid * BPT + j] = run;
                 run += bc[j];
             }
         }
         __syncthreads();
-        for (uint32_t i = tid; i < n; i += LP_NT) {
+        for (uint32_t i = tid; i < n; i += NT) {
             const K v = A[i];
             B[atomicAdd(&s_cnt1[key_digit(v, s1, LS_B1 - 1)], 1u)] = v;
         }
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
         // small bin the key counts its equals and emits at the first of them;
         // in a larger bin it only marks whether it equals the bin's first key,
         // and the bin's first key lists the bin
-        for (uint32_t i0 = 0; i0 < n; i0 += LP_NT) {
+        for (uint32_t i0 = 0; i0 < n; i0 += NT) {
             const uint32_t i = i0 + tid;
             bool head = false, eqf = false;
             uint32_t cnt = 0;
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
             const int nl = s_nl;
             // one warp per larger bin: the first key's count is a popcount of
             // the mask, the other keys are compacted into A and counted there
-            for (int q = warp; q < nl; q += LP_NT / 32) {
+            for (int q = warp; q < nl; q += NT / 32) {
                 const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
                 const uint32_t w0 = bs >> 5, w1 = (be - 1) >> 5;
                 uint32_t c1 = 0;
@@ -635,17 +637,17 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
             }
             K* X = bin.buf ? B : A;
             K* Y = bin.buf ? A : B;
-            s_cnt[tid] = 0;
+            if (tid < 256) s_cnt[tid] = 0;
             __syncthreads();
-            for (uint32_t i = tid; i < bin.len; i += LP_NT)
+            for (uint32_t i = tid; i < bin.len; i += NT)
                 atomicAdd(&s_cnt[key_digit(X[bin.beg + i], bin.shift, 0xFF)], 1u);
             __syncthreads();
-            const uint32_t cnt = s_cnt[tid];
+            const uint32_t cnt = tid < 256 ? s_cnt[tid] : 0u;  // sub-bin (digit) tid
             uint32_t t2;
-            const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, t2);
-            s_cur[tid] = ex;
+            const uint32_t ex = block_excl_sum<NT, uint32_t>(cnt, s_scr32, t2);
+            if (tid < 256) s_cur[tid] = ex;
             __syncthreads();
-            for (uint32_t i = tid; i < bin.len; i += LP_NT) {
+            for (uint32_t i = tid; i < bin.len; i += NT) {
                 const K v = X[bin.beg + i];
                 Y[bin.beg + atomicAdd(&s_cur[key_digit(v, bin.shift, 0xFF)], 1u)] = v;
             }
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
                 s_list[atomicAdd(&s_nl, 1)] = sb | (cnt << 16);
             __syncthreads();
             const int nl2 = s_nl;
-            for (int q = warp; q < nl2; q += LP_NT / 32)
+            for (int q = warp; q < nl2; q += NT / 32)
                 warp_bin<Cfg::STACK>(Y, X, s_list[q] & 0xFFFFu, s_list[q] >> 16, bin.shift > 8 ? bin.shift - 8 : 0,
                                      bin.shift == 0, bin.buf ^ 1, s_stack, &s_sp, &s_abort, err, emit);
             __syncthreads();
@@ -669,7 +671,7 @@ __global__ void __launch_bounds__(LP_NT, BIG ? 1 : 3) k_local_sort(const u64* __
     }
     if (my_ones) atomicAdd(&s_hist[1], my_ones);  // hist_len >= 2: count 1 has its own bin
     __syncthreads();
-    for (uint32_t i = tid; i < hs; i += LP_NT)
+    for (uint32_t i = tid; i < hs; i += NT)
         if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(hist + i), (unsigned long long)s_hist[i]);
     // per-CTA totals
     my_distinct = warp_incl_sum<u64>(my_distinct);
@@ -692,12 +694,13 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
     auto go = [&](auto kern, auto* kp) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, LP_NT, dyn);
+        const int nt = big ? 512 : 256;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, dyn);
         if (occ < 1) occ = 1;
         uint64_t want = n_sub;
         uint64_t g = (uint64_t)num_sms * occ;
         if (want < g) g = want;
-        kern<<<(unsigned)g, LP_NT, dyn, st>>>((const u64*)sub_off, only, n_sub, shift0, kp, kcount, kc, ov_list,
+        kern<<<(unsigned)g, nt, dyn, st>>>((const u64*)sub_off, only, n_sub, shift0, kp, kcount, kc, ov_list,
                                               (unsigned long long*)ov_stats, lo, hi, (u64*)hist, hist_len,
                                               max_count, (unsigned long long*)n_distinct, claim, err);
     };
