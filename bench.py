@@ -12,8 +12,9 @@ steps.
 
 Printed JSON line: value = k-mers counted / s over all ranks; e2e = the same
 through hsk_count() with pinned host buffers (copies inside the timed region);
-roofline = the dominant kernel (the onesweep radix pass) against the measured
-HBM copy bandwidth; cpu_baseline = the CPU oracle on a bounded sample.  On one
+roofline = the dominant kernel (the on-chip sub-segment sort, bound by
+instruction issue; with local_sort off, the onesweep radix pass against the
+measured HBM copy bandwidth); cpu_baseline = the CPU oracle on a bounded sample.  On one
 GPU the line also carries "batched" (256 independent read sets through
 hsk_count_batch against the same sets run one by one through hsk_count) and
 "served" (a Poisson request stream through hsk_submit/hsk_wait: throughput
@@ -42,10 +43,16 @@ sys.path.insert(0, ROOT)
 METRIC = "k-mers counted/s at k=31 on 1 GB300 (plain vs batched/served); p50/p99 job latency"
 UNIT = "k-mers/s"
 
-# DRAM bytes (read + write) per onesweep launch from one ncu capture, keyed by
-# workload and the SHA-256 of the radix-pass source at capture time; reported
-# only while that source is unchanged.
-NCU_TRAFFIC = {}
+# Per-key counters of the dominant kernel from one ncu capture, keyed by the
+# workload and the SHA-256 (first 16 hex digits) of the kernel's source file
+# at capture time; used only while that source is unchanged.
+#   inst  : warp instructions issued per key (both on-chip passes)
+#   dram  : DRAM bytes read + written per key (both passes)
+# The commands that produced them are in profiles/.
+NCU_PER_KEY = {}
+# Issue slots of one GB300: 152 SMs x 4 warp schedulers x 1 warp instruction
+# per cycle (times the SM clock sampled during the run).
+ISSUE_SLOTS_PER_CYCLE = 152 * 4
 
 
 def source_sha(path: str) -> str:
@@ -412,20 +419,41 @@ def main():
     # roofline of the dominant kernel
     peaks = measured_peaks()
     kb = 8 * kw
-    if passes > 0:  # global radix passes: one onesweep LSD pass reads and writes every key
-        kernel = "k_onesweep_tma (8-bit LSD pass)"
-        src = "k_sort.cu"
+    clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    if passes > 0:  # global radix passes: one onesweep LSD pass reads and writes every key (HBM-bound)
         launch_ms = stage_ms[4] / passes
         bytes_per_launch = n_windows * 2 * kb
-    else:           # on-chip path: the sub-segment sort reads every key once, writes the kept pairs
-        kernel = "k_local_sort (sub-segment sort + count in shared memory)"
-        src = "k_local.cu"
+        achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+        sha = source_sha(os.path.join(ROOT, "paper_2407_07718_gb300", "csrc", "k_sort.cu"))
+        cnt = NCU_PER_KEY.get((args.workload, sha))
+        roofline = {"bound": "hbm", "kernel": "k_onesweep_tma (8-bit LSD pass)", "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": cnt["dram"] * n_windows / passes if cnt else None,
+                    "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs copy bandwidth)",
+                    "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms}
+    else:
+        # on-chip path: the sub-segment sort (k_local_sort, both passes) reads
+        # every key once and writes the kept pairs; it is bound by instruction
+        # issue and shared-memory latency, so its roofline is the issue rate
         launch_ms = stage_ms[4] / args.steps
-        bytes_per_launch = n_windows * kb + int(res.n_pairs) * (kb + 4)
-    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
-    sha = source_sha(os.path.join(ROOT, "paper_2407_07718_gb300", "csrc", src))
-    traffic = NCU_TRAFFIC.get((args.workload, sha))
-    # end-to-end algorithmic bytes per window (byte model of the whole path)
+        sha = source_sha(os.path.join(ROOT, "paper_2407_07718_gb300", "csrc", "k_local.cu"))
+        cnt = NCU_PER_KEY.get((args.workload, sha))
+        peak_issue = ISSUE_SLOTS_PER_CYCLE * clk_mhz / 1e3  # G warp-instructions / s
+        inst = cnt["inst"] * n_windows if cnt else None
+        achieved = inst / (launch_ms / 1e3) / 1e9 if inst and launch_ms > 0 else None
+        hbm_bytes = n_windows * kb + int(res.n_pairs) * (kb + 4)
+        hbm_achieved = hbm_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": "k_local_sort (sub-segment sort + count in shared memory, both passes)",
+                    "achieved": achieved, "peak": peak_issue, "unit": "G warp-instructions/s",
+                    "frac": achieved / peak_issue if achieved else None,
+                    "traffic": cnt["dram"] * n_windows if cnt else None,
+                    "peak_source": f"issue slots: 152 SMs x 4 schedulers x {clk_mhz:.0f} MHz (sampled)",
+                    "inst_per_launch": inst, "launch_ms": launch_ms,
+                    "hbm_view": {"bytes_per_launch": hbm_bytes, "achieved": hbm_achieved, "unit": "GB/s",
+                                 "frac": hbm_achieved / peaks["hbm_gbs"],
+                                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs copy bandwidth)"}}
+    roofline["passes_per_step"] = passes / args.steps
+    # end-to-end algorithmic bytes per step (byte model of the whole path)
     n_sm = int(res.n_supermers)
     rec_b = 16 if kw == 1 else 32
     P = (2 * rs.k + 7) // 8
@@ -443,29 +471,24 @@ def main():
                  + s45
                  + int(res.n_pairs) * (kb + 4) * 2 * P)    # S6: output pairs sorted
     step_s = ms_max / args.steps / 1e3
-    roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": traffic, "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs copy bandwidth)",
-                "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms, "passes_per_step": passes / args.steps,
-                "end_to_end": {"bytes_per_step": e2e_bytes, "achieved": e2e_bytes / step_s / 1e9,
-                               "frac": e2e_bytes / step_s / 1e9 / peaks["hbm_gbs"]}}
+    roofline["end_to_end"] = {"bytes_per_step": e2e_bytes, "achieved": e2e_bytes / step_s / 1e9,
+                              "frac": e2e_bytes / step_s / 1e9 / peaks["hbm_gbs"]}
 
     # end to end through the host API: pinned inputs, results copied back
-    e2e = None
-    if rank == 0 or True:
-        pin_reads = torch.from_numpy(rs.reads).pin_memory().numpy()
-        pin_offs = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
-        r = ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi)  # warm
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            r = ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi)
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        dt = reduce_max(pg, dt, dev)
-        e2e = {"value": reduce_sum(pg, float(r.n_windows), dev) / dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(pin_reads.nbytes + pin_offs.nbytes),
-               "d2h_bytes_per_step": int(r.kmers.nbytes + r.counts.nbytes + r.hist.nbytes),
-               "ms_per_step": dt * 1e3}
-        assert r.n_windows == n_windows
+    # (every rank: its replica's time enters the max over ranks)
+    pin_reads = torch.from_numpy(rs.reads).pin_memory().numpy()
+    pin_offs = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    r = ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi)  # warm
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        r = ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi)
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    dt = reduce_max(pg, dt, dev)
+    e2e = {"value": reduce_sum(pg, float(r.n_windows), dev) / dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(pin_reads.nbytes + pin_offs.nbytes),
+           "d2h_bytes_per_step": int(r.kmers.nbytes + r.counts.nbytes + r.hist.nbytes),
+           "ms_per_step": dt * 1e3}
+    assert r.n_windows == n_windows
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -45,8 +45,10 @@ int hsk_stage_encode(hsk_ctx* ctx, const char* d_reads, uint64_t n_bases,
  * every window start g in [0, n_bases): d_valid[g] = 1 if bases g..g+k-1 are
  * all ACGT and inside one read, else 0; for valid windows d_key[2g], d_key[2g+1]
  * = {lo, hi} of the canonical 2k-bit code and d_minhash[g] = the minimum over
- * the window's k-m+1 m-mers of fmix64(canonical m-mer XOR seed).  Entries of
- * invalid windows are unspecified.  Outputs caller-allocated: n_bases,
+ * the window's k-m+1 m-mers of their score, fmix32(lo32 ^ hi32 ^ seed32) with
+ * lo32/hi32 the low and high 32-bit halves of the canonical m-mer code and
+ * seed32 the low half of the context's seed (MurmurHash3's 32-bit
+ * finalizer).  Entries of invalid windows are unspecified.  Outputs caller-allocated: n_bases,
  * 2*n_bases and n_bases elements. */
 int hsk_stage_windows(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offsets,
                       uint64_t n_reads, uint64_t n_bases, int k, int m, uint8_t* d_valid,

@@ -117,24 +117,6 @@ __device__ __forceinline__ u64 mask_bits(const u64* w, u64 p, int n) {
     return n >= 64 ? v : (v >> (64 - n));
 }
 
-// MurmurHash3's 64-bit finalizer (A. Appleby, public domain): the m-mer score
-// of Sec. 3.2.
-__device__ __forceinline__ u64 fmix64(u64 h) {
-    h ^= h >> 33;
-    h *= 0xff51afd7ed558ccdULL;
-    h ^= h >> 33;
-    h *= 0xc4ceb9fe1a85ec53ULL;
-    h ^= h >> 33;
-    return h;
-}
-
-// Bucket (task) of a minimizer score: the remainder of the score divided by
-// the number of buckets (Sec. 3.2); n_buckets is a power of two, so the
-// remainder is a mask of the low bits.
-__device__ __forceinline__ uint32_t bucket_of(u64 score, uint32_t n_buckets) {
-    return (uint32_t)score & (n_buckets - 1u);
-}
-
 // ---------------------------------------------------------------------------
 // device error flag and bounded waits
 // ---------------------------------------------------------------------------

@@ -596,11 +596,58 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
         }
         __syncthreads();
         {
+            // ---- larger bins of <= LS_MED keys.  Their keys that differ from
+            // the bin's first key are few (sequencing-error variants of a
+            // k-mer that shares the bin's digits): each counts its equals
+            // among them through the mask's zero bits, key by key in parallel.
+            // The first key's count is a popcount of the mask, one thread per bin.
+            for (uint32_t i0 = 0; i0 < n; i0 += NT) {
+                const uint32_t i = i0 + tid;
+                bool head = false;
+                uint32_t cnt = 0;
+                K v{};
+                if (i < n && !((s_eqf[i >> 5] >> (i & 31)) & 1u)) {
+                    v = B[i];
+                    const uint32_t d = key_digit(v, s1, LS_B1 - 1);
+                    const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
+                    if (be - bs > (uint32_t)LS_SMALL && be - bs <= (uint32_t)LS_MED) {
+                        head = true;
+                        const uint32_t w0 = bs >> 5, w1 = (be - 1) >> 5;
+                        for (uint32_t w = w0; w <= w1; ++w) {
+                            uint32_t zm = ~s_eqf[w];
+                            if (w == w0) zm &= 0xFFFFFFFFu << (bs & 31);
+                            if (w == w1 && ((be - 1) & 31) != 31) zm &= (2u << ((be - 1) & 31)) - 1u;
+                            for (; zm; zm &= zm - 1) {
+                                const uint32_t j = w * 32 + (uint32_t)(__ffs(zm) - 1);
+                                if (key_eq(B[j], v)) {
+                                    ++cnt;
+                                    head = head && j >= i;
+                                }
+                            }
+                        }
+                    }
+                }
+                emit_warp(head, v, cnt);
+            }
             const int nl = s_nl;
-            // one warp per larger bin: the first key's count is a popcount of
-            // the mask, the other keys are compacted into A and counted there
+            for (int q = tid; q < nl; q += NT) {
+                const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
+                if (len > (uint32_t)LS_MED) continue;
+                uint32_t c1 = 0;
+                for (uint32_t w = bs >> 5; w <= (be - 1) >> 5; ++w) {
+                    uint32_t m = s_eqf[w];
+                    if (w == bs >> 5) m &= 0xFFFFFFFFu << (bs & 31);
+                    if (w == (be - 1) >> 5 && ((be - 1) & 31) != 31) m &= (2u << ((be - 1) & 31)) - 1u;
+                    c1 += (uint32_t)__popc(m);
+                }
+                emit(B[bs], c1);
+            }
+            // ---- bins of more than LS_MED keys: one warp each; the first
+            // key's copies counted from the mask, the other keys compacted into
+            // A and counted there
             for (int q = warp; q < nl; q += NT / 32) {
                 const uint32_t bs = s_list[q] & 0xFFFFu, len = s_list[q] >> 16, be = bs + len;
+                if (len <= (uint32_t)LS_MED) continue;
                 const uint32_t w0 = bs >> 5, w1 = (be - 1) >> 5;
                 uint32_t c1 = 0;
                 for (uint32_t w = w0 + lane; w <= w1; w += 32) {
@@ -613,8 +660,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                 if (lane == 0) emit(B[bs], c1);
                 if (c1 == len) continue;
                 uint32_t kept = 0;
-                for (uint32_t i0 = 0; i0 < len; i0 += 32) {
-                    const uint32_t i = bs + i0 + lane;
+                for (uint32_t j0 = 0; j0 < len; j0 += 32) {
+                    const uint32_t i = bs + j0 + lane;
                     const bool rest = i < be && !((s_eqf[i >> 5] >> (i & 31)) & 1u);
                     const uint32_t rm = __ballot_sync(0xffffffffu, rest);
                     if (rest) A[bs + kept + (uint32_t)__popc(rm & ((1u << lane) - 1u))] = B[i];
