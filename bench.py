@@ -49,7 +49,11 @@ UNIT = "k-mers/s"
 #   inst  : warp instructions issued per key (both on-chip passes)
 #   dram  : DRAM bytes read + written per key (both passes)
 # The commands that produced them are in profiles/.
-NCU_PER_KEY = {}
+NCU_PER_KEY = {
+    # long-read workload, k=31: k_local_sort passes 0 + 1, smsp__inst_executed.sum at full
+    # size (1.4955 G keys); DRAM bytes from the 0.1-scale case (149.6 M keys), per key
+    ("long_read", "8fca31599648b42d"): {"inst": 11.7591, "dram": 8.3595},
+}
 # Issue slots of one GB300: 152 SMs x 4 warp schedulers x 1 warp instruction
 # per cycle (times the SM clock sampled during the run).
 ISSUE_SLOTS_PER_CYCLE = 152 * 4
