@@ -34,9 +34,10 @@ constexpr int SM_TW = 32 * SM_STEPS;      // windows per warp tile
 constexpr int SM_PW = SM_TW / 32 + 6;     // packed words staged per warp (even)
 constexpr int SM_MW = SM_TW / 64 + 4;     // mask words staged per warp (even)
 constexpr int SM_DBUF = 128;              // descriptors buffered per warp
+constexpr int SM_VW = SM_TW / 64;         // valid-window words per warp
 
 size_t supermer_smem_bytes(int mode, uint32_t n_buckets) {
-    size_t s = (size_t)SM_WARPS * (SM_PW + 2 * SM_MW) * sizeof(u64);
+    size_t s = (size_t)SM_WARPS * (SM_PW + 2 * SM_MW + SM_VW) * sizeof(u64);
     if (mode == SM_DESC) s += (size_t)SM_WARPS * SM_DBUF * sizeof(u64) + (size_t)n_buckets * 2 * sizeof(uint32_t);
     return s;
 }
@@ -94,6 +95,21 @@ __device__ __forceinline__ uint32_t window_min(const uint32_t (&X)[NREG], int w,
     return d == 0 ? A[0] : min(A[0], seq_at<NREG>(A, 0, d, lane));
 }
 
+// Bit t (most significant first) = OR of bits [t, t + L) of the 128-bit
+// value a:b, for t = 0..63 and 1 <= L <= 64: OR over windows of doubling
+// width, then two overlapping windows of that width.
+__device__ __forceinline__ u64 window_or64(u64 a, u64 b, int L) {
+    u64 hi = a, lo = b;
+    int width = 1;
+    while (2 * width <= L) {
+        hi |= (hi << width) | (lo >> (64 - width));
+        lo |= lo << width;
+        width *= 2;
+    }
+    const int d = L - width;  // 0 <= d < width
+    return d ? hi | (hi << d) | (lo >> (64 - d)) : hi;
+}
+
 __device__ __forceinline__ int warp_incl_max(int v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -122,7 +138,8 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
     u64* s_pk = reinterpret_cast<u64*>(smem);
     u64* s_iv = s_pk + SM_WARPS * SM_PW;
     u64* s_rs = s_iv + SM_WARPS * SM_MW;
-    u64* s_desc = s_rs + SM_WARPS * SM_MW;                                       // DESC
+    u64* s_val = s_rs + SM_WARPS * SM_MW;
+    u64* s_desc = s_val + SM_WARPS * SM_VW;                                      // DESC
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_desc + SM_WARPS * SM_DBUF);  // DESC
     uint32_t* s_km = s_cnt + P.n_buckets;                                        // DESC
 
@@ -138,6 +155,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
     u64* wpk = s_pk + warp * SM_PW;
     u64* wiv = s_iv + warp * SM_MW;
     u64* wrs = s_rs + warp * SM_MW;
+    u64* wval = s_val + warp * SM_VW;
     u64* wdesc = s_desc + warp * SM_DBUF;
     int nbuf = 0;  // descriptors buffered by this warp (warp-uniform)
     const u64 n_tiles = (P.n_bases + SM_TW - 1) / SM_TW;
@@ -183,6 +201,19 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
                 wrs[2 * i + 1] = b.y;
             }
             __syncwarp();
+            // window starts of the tile whose k bases are all valid and in one
+            // read: no invalid base in [p, p+k), no read start in (p, p+k)
+            if (lane < SM_TW / 64) {
+                const int o = lane;
+                u64 bad = window_or64(wiv[o], wiv[o + 1], k);
+                if (k > 1) {
+                    const u64 a = (wrs[o] << 1) | (wrs[o + 1] >> 63);
+                    const u64 b = (wrs[o + 1] << 1) | (wrs[o + 2] >> 63);
+                    bad |= window_or64(a, b, k - 1);
+                }
+                wval[o] = ~bad;
+            }
+            __syncwarp();
         }
 
         // rolling m-mer scores: X[r] = score at local base 32*(s + r) + lane
@@ -216,8 +247,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
         for (int s = 0; s < SM_STEPS; ++s) {
             const int lp = 32 * s + lane;
             const u64 p = p0 + lp;
-            int valid = (p + k <= P.n_bases) && mask_bits(wiv, lp, k) == 0 &&
-                        (k == 1 || mask_bits(wrs, lp + 1, k - 1) == 0);
+            int valid = (p + k <= P.n_bases) && ((wval[lp >> 6] >> (63 - (lp & 63))) & 1);
             const uint32_t mh = window_min<NREG>(X, w, lane);
             const uint32_t b = mh & (B - 1u);
 
