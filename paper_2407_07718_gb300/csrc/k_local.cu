@@ -568,7 +568,9 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
         // ---- every key: its bin is [end of bin d-1, end of bin d).  In a
         // small bin the key counts its equals and emits at the first of them;
         // in a larger bin it only marks whether it equals the bin's first key,
-        // and the bin's first key lists the bin
+        // and the bin's first key lists the bin.  The mask bit is set for the
+        // small bins' keys too, so its zero bits are exactly the larger bins'
+        // keys that differ from their bin's first key
         for (uint32_t i0 = 0; i0 < n; i0 += NT) {
             const uint32_t i = i0 + tid;
             bool head = false, eqf = false;
@@ -580,6 +582,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                 const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
                 if (be - bs <= (uint32_t)LS_SMALL) {
                     head = true;
+                    eqf = true;  // counted here: the mask marks it done
                     for (uint32_t j = bs; j < be; ++j)
                         if (key_eq(B[j], v)) {
                             ++cnt;
@@ -659,13 +662,22 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                 for (int o = 16; o > 0; o >>= 1) c1 += __shfl_xor_sync(0xffffffffu, c1, o);
                 if (lane == 0) emit(B[bs], c1);
                 if (c1 == len) continue;
+                // the keys at the mask's zero bits, compacted: each lane takes
+                // one mask word, a warp scan of the words' counts places them
                 uint32_t kept = 0;
-                for (uint32_t j0 = 0; j0 < len; j0 += 32) {
-                    const uint32_t i = bs + j0 + lane;
-                    const bool rest = i < be && !((s_eqf[i >> 5] >> (i & 31)) & 1u);
-                    const uint32_t rm = __ballot_sync(0xffffffffu, rest);
-                    if (rest) A[bs + kept + (uint32_t)__popc(rm & ((1u << lane) - 1u))] = B[i];
-                    kept += (uint32_t)__popc(rm);
+                for (uint32_t wb = w0; wb <= w1; wb += 32) {
+                    const uint32_t w = wb + lane;
+                    uint32_t zm = 0;
+                    if (w <= w1) {
+                        zm = ~s_eqf[w];
+                        if (w == w0) zm &= 0xFFFFFFFFu << (bs & 31);
+                        if (w == w1 && ((be - 1) & 31) != 31) zm &= (2u << ((be - 1) & 31)) - 1u;
+                    }
+                    const uint32_t nz = (uint32_t)__popc(zm);
+                    const uint32_t incl = warp_incl_sum<uint32_t>(nz);
+                    uint32_t at = bs + kept + incl - nz;
+                    for (; zm; zm &= zm - 1) A[at++] = B[w * 32 + (uint32_t)(__ffs(zm) - 1)];
+                    kept += __shfl_sync(0xffffffffu, incl, 31);
                 }
                 __syncwarp();
                 warp_bin<Cfg::STACK>(A, B, bs, kept, s2, s1 == 0, 0, s_stack, &s_sp, &s_abort, err, emit);
