@@ -17,7 +17,8 @@
 // the window minimum over w = k-m+1 scores comes from a log-step doubling of
 // minima across lanes with shuffles (a sparse table in registers).  Supermer
 // cuts (bucket change, invalid window, cap of nmax k-mers, tile end) come
-// from a warp max-scan of run starts.  The walk runs once (DESC): every
+// from ballots of run starts (the latest start at or before a lane is the
+// highest set bit below it).  The walk runs once (DESC): every
 // supermer becomes an 8-byte descriptor (start base, k-mer count, bucket),
 // buffered per warp in shared memory and appended to a global list with one
 // atomic per buffer; per-bucket record and k-mer counts are kept in shared
@@ -108,16 +109,6 @@ __device__ __forceinline__ u64 window_or64(u64 a, u64 b, int L) {
     }
     const int d = L - width;  // 0 <= d < width
     return d ? hi | (hi << d) | (lo >> (64 - d)) : hi;
-}
-
-__device__ __forceinline__ int warp_incl_max(int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v = v > o ? v : o;
-    }
-    return v;
 }
 
 // Bits [2*nb, 64) of word x cleared when the record holds only nb (< 32) more bases.
@@ -223,8 +214,8 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
 
         int c_valid = 0, c_runstart = -1;   // carry from lane 31 of the previous step
         uint32_t c_b = 0;
-        int pv = 0, pstart = 0, plp = 0, psm = 0;  // previous step, for delayed emission
-        uint32_t pb = 0;
+        int pv = 0, plp = 0, psm = 0;       // previous step, for delayed emission
+        uint32_t pb = 0, pvmask = 0, psmask = 0;
 
         // emit the supermers that end in the previous step (end = valid and the
         // next window is invalid or starts a new supermer)
@@ -267,36 +258,35 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
                     }
                 }
             } else {
-                int prev_valid = __shfl_up_sync(0xffffffffu, valid, 1);
+                // flags of neighbouring lanes come from ballots; only the
+                // bucket of the lane before needs a shuffle
+                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
                 uint32_t prev_b = __shfl_up_sync(0xffffffffu, b, 1);
-                if (lane == 0) {
-                    prev_valid = c_valid;
-                    prev_b = c_b;
-                }
-                int start0 = valid && !(prev_valid && prev_b == b);
-                int rs = warp_incl_max(start0 ? lp : -1);
-                rs = rs > c_runstart ? rs : c_runstart;
+                int prev_valid = lane ? (int)((vmask >> (lane - 1)) & 1u) : c_valid;
+                if (lane == 0) prev_b = c_b;
+                const int start0 = valid && !(prev_valid && prev_b == b);
+                // the latest run start at or before this window
+                const uint32_t smask0 = __ballot_sync(0xffffffffu, start0);
+                const uint32_t le = smask0 & (0xFFFFFFFFu >> (31 - lane));
+                const int rs = le ? 32 * s + (31 - __clz(le)) : c_runstart;
                 const int pos_in_run = lp - rs;
                 // pos_in_run / nmax by a multiply: exact for pos_in_run < 2^24
                 const int q = (int)__umulhi((uint32_t)pos_in_run, P.nmax_magic);
                 const int start = valid && (start0 || pos_in_run == q * nmax);
                 const int smstart = rs + q * nmax;
+                const uint32_t smask = __ballot_sync(0xffffffffu, start);
                 if (s > 0) {
-                    int nv = __shfl_down_sync(0xffffffffu, pv, 1);
-                    int ns = __shfl_down_sync(0xffffffffu, pstart, 1);
-                    int v0 = __shfl_sync(0xffffffffu, valid, 0);
-                    int s0 = __shfl_sync(0xffffffffu, start, 0);
-                    if (lane == 31) {
-                        nv = v0;
-                        ns = s0;
-                    }
+                    // the window after this lane's window of the previous step
+                    const int nv = lane < 31 ? (int)((pvmask >> (lane + 1)) & 1u) : (int)(vmask & 1u);
+                    const int ns = lane < 31 ? (int)((psmask >> (lane + 1)) & 1u) : (int)(smask & 1u);
                     emit_prev(nv, ns);
                 }
-                c_valid = __shfl_sync(0xffffffffu, valid, 31);
+                c_valid = (int)(vmask >> 31);
                 c_b = __shfl_sync(0xffffffffu, b, 31);
-                c_runstart = __shfl_sync(0xffffffffu, rs, 31);
+                if (smask0) c_runstart = 32 * s + (31 - __clz(smask0));
                 pv = valid;
-                pstart = start;
+                pvmask = vmask;
+                psmask = smask;
                 pb = b;
                 plp = lp;
                 psm = smstart;
@@ -307,12 +297,8 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
             X[NREG - 1] = mmer_score(wpk, 32 * (s + NREG) + lane, m, P.seed32);
         }
         if (MODE != SM_DUMP) {  // the tile edge ends every open supermer
-            int nv = __shfl_down_sync(0xffffffffu, pv, 1);
-            int ns = __shfl_down_sync(0xffffffffu, pstart, 1);
-            if (lane == 31) {
-                nv = 0;
-                ns = 0;
-            }
+            const int nv = lane < 31 ? (int)((pvmask >> (lane + 1)) & 1u) : 0;
+            const int ns = lane < 31 ? (int)((psmask >> (lane + 1)) & 1u) : 0;
             emit_prev(nv, ns);
         }
         __syncwarp();
