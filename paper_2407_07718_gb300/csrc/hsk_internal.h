@@ -23,6 +23,11 @@ void count_launch(unsigned n = 1);
 // ---- S1 encode ----------------------------------------------------------
 void launch_encode(const char* reads, uint64_t n_bases, uint64_t* packed, uint64_t* invalid,
                    uint64_t n_packed_words, uint64_t n_mask_words, cudaStream_t st);
+// bases [b0, b1) only (b0 a multiple of 64)
+void launch_encode_range(const char* reads, uint64_t n_bases, uint64_t b0, uint64_t b1, uint64_t* packed,
+                         uint64_t* invalid, uint64_t n_packed_words, cudaStream_t st);
+constexpr uint64_t SM_TILE_BASES = 1024;   // windows per S2 warp tile
+constexpr uint64_t SM_TILE_REACH = 1280;   // bases past a tile's start that its walk reads
 void launch_mark_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,
                         uint64_t* start_mask, int* err, cudaStream_t st);
 
@@ -42,6 +47,7 @@ struct SmParams {
     uint32_t nmax_magic;      // ceil(2^32 / nmax): q = umulhi(x, magic) = x / nmax for x < 2^24
     int rec_words;            // 2 (k <= 32) or 4 (k <= 64)
     uint32_t grid;
+    uint64_t tile_begin, tile_end;     // warp tiles [begin, end) of 1024 windows (end 0 = all)
     uint64_t* desc;                    // supermer descriptors (DESC)
     uint64_t desc_cap;
     unsigned long long* desc_count;    // descriptors produced (may exceed desc_cap)

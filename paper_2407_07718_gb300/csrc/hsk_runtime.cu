@@ -154,6 +154,9 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
     cudaError_t e = cudaSetDevice(cfg.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg.device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
+    for (int i = 0; i < HSK_MAX_PIPE && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&c->pipe_ev[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     size_t free_b = 0, total_b = 0;
@@ -190,6 +193,12 @@ extern "C" void hsk_destroy(hsk_ctx* c) {
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->cstream) {
+        cudaStreamSynchronize(c->cstream);
+        cudaStreamDestroy(c->cstream);
+    }
+    for (int i = 0; i < HSK_MAX_PIPE; ++i)
+        if (c->pipe_ev[i]) cudaEventDestroy(c->pipe_ev[i]);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     delete c;
 }
@@ -316,7 +325,7 @@ static int read_device_error(hsk_ctx* c, cudaStream_t st, uint32_t* max_count = 
 // ---------------------------------------------------------------------------
 int hsk_encode_into(hsk_ctx* c, const char* d_reads, uint64_t n_bases, const uint64_t* d_offsets,
                     uint64_t n_reads, DevBuf& pk, DevBuf& iv, DevBuf& rs, Encoded& E,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool defer_bases) {
     E.n_bases = n_bases;
     E.n_pw = (n_bases + 31) / 32;
     E.n_mw = (n_bases + 63) / 64;
@@ -327,7 +336,8 @@ int hsk_encode_into(hsk_ctx* c, const char* d_reads, uint64_t n_bases, const uin
     CK(cudaMemsetAsync((uint64_t*)iv.p + E.n_mw, 0, 8 * 8, st));
     CK(cudaMemsetAsync(rs.p, 0, (E.n_mw + 8) * 8, st));
     launch_mark_starts(d_offsets, n_reads, n_bases, (uint64_t*)rs.p, c->d_err, st);
-    launch_encode(d_reads, n_bases, (uint64_t*)pk.p, (uint64_t*)iv.p, E.n_pw, E.n_mw, st);
+    // with defer_bases the bases are encoded chunk by chunk as they arrive (hsk_supermers)
+    if (!defer_bases) launch_encode(d_reads, n_bases, (uint64_t*)pk.p, (uint64_t*)iv.p, E.n_pw, E.n_mw, st);
     CK(cudaGetLastError());
     E.packed = (const uint64_t*)pk.p;
     E.invalid = (const uint64_t*)iv.p;
@@ -366,7 +376,7 @@ static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t 
 
 // Count supermers per (bucket, CTA), scan to record offsets, scatter records.
 int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S,
-                  cudaStream_t st) {
+                  cudaStream_t st, InputPipe* pipe) {
     SmParams P;
     fill_sm_params(c, E, k, m, B, P);
     const bool wide = k > 32;
@@ -395,7 +405,36 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
         P.desc_count = (unsigned long long*)c->d_ndesc;
         P.bucket_rec = d_rec_cnt;
         P.bucket_kmers = (uint64_t*)c->bucket_kmers.p;
-        launch_supermer(SM_DESC, P, st);
+        if (pipe && attempt == 0) {
+            // chunk i's bytes arrive on the copy stream: encode them, then walk
+            // every tile whose staged bases are now encoded; the next copy is
+            // issued before this chunk's work is queued (a pageable copy
+            // returns only once staged, and the GPU works meanwhile)
+            const uint64_t n_tiles = (E.n_bases + SM_TILE_BASES - 1) / SM_TILE_BASES;
+            uint64_t t_done = 0;
+            const uint32_t grid = P.grid;
+            for (int i = 0; i < pipe->n; ++i) {
+                while (pipe->issued < pipe->n && pipe->issued <= i + 1) CK(pipe->issue(pipe->issued++));
+                CK(cudaStreamWaitEvent(st, pipe->ev[i], 0));
+                launch_encode_range(pipe->d_reads, E.n_bases, pipe->bound[i], pipe->bound[i + 1],
+                                    (uint64_t*)E.packed, (uint64_t*)E.invalid, E.n_pw, st);
+                const uint64_t b = pipe->bound[i + 1];
+                uint64_t t_end = i + 1 == pipe->n ? n_tiles
+                                 : (b >= SM_TILE_REACH ? (b - SM_TILE_REACH) / SM_TILE_BASES + 1 : 0);
+                if (t_end > n_tiles) t_end = n_tiles;
+                if (t_end > t_done) {
+                    P.tile_begin = t_done;
+                    P.tile_end = t_end;
+                    P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(grid, (t_end - t_done + 7) / 8));
+                    launch_supermer(SM_DESC, P, st);
+                    t_done = t_end;
+                }
+            }
+            P.tile_begin = P.tile_end = 0;
+            P.grid = grid;
+        } else {
+            launch_supermer(SM_DESC, P, st);
+        }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&n_desc, c->d_ndesc, 8, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -757,7 +796,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
 
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
-                  DevResult& R) {
+                  DevResult& R, InputPipe* pipe) {
     memset(&R, 0, sizeof(R));
     c->zst = st;
     if (n_bases >= (1ull << 40)) {
@@ -777,11 +816,11 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     prof_mark(c, st, -1);
     Output O;
     Encoded E;
-    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
+    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, pipe != nullptr));
     prof_mark(c, st, 0);
     Supermers S;
     uint32_t B = hsk_pick_buckets(c, n_bases, k);
-    TRY(hsk_supermers(c, E, k, m, B, S, st));
+    TRY(hsk_supermers(c, E, k, m, B, S, st, pipe));
     prof_mark(c, st, 2);
     R.n_windows = S.n_kmers;
     R.n_supermers = S.n_records;
@@ -932,12 +971,35 @@ int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, ui
     }
     TRY(hsk_ensure(c, d_reads, n_bases + 16, false));
     TRY(hsk_ensure(c, d_offsets, (n_reads + 1) * 8, false));
-    if (n_bases) CK(cudaMemcpyAsync(d_reads.p, reads, n_bases, cudaMemcpyHostToDevice, st));
     if (n_reads) CK(cudaMemcpyAsync(d_offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, st));
     else CK(cudaMemsetAsync(d_offsets.p, 0, 8, st));
+    // large inputs: the read bytes arrive in chunks on the copy stream while
+    // S1/S2 work on the chunks already there
+    InputPipe pipe;
+    InputPipe* pp = nullptr;
+    if (n_bases >= (64ull << 20) && c->cstream) {
+        const int n = (int)std::min<uint64_t>(HSK_MAX_PIPE, std::max<uint64_t>(2, n_bases >> 27));
+        pipe.n = n;
+        for (int i = 0; i < n; ++i) pipe.bound[i] = ((uint64_t)i * n_bases / n) & ~0xFFFFull;
+        pipe.bound[n] = n_bases;
+        for (int i = 0; i < n; ++i) pipe.ev[i] = c->pipe_ev[i];
+        pipe.h_reads = reads;
+        pipe.d_reads = (char*)d_reads.p;
+        pipe.cs = c->cstream;
+        pp = &pipe;
+    } else if (n_bases) {
+        CK(cudaMemcpyAsync(d_reads.p, reads, n_bases, cudaMemcpyHostToDevice, st));
+    }
     DevResult R;
-    TRY(hsk_run_count(c, (const char*)d_reads.p, (const uint64_t*)d_offsets.p, n_reads, n_bases, k,
-                      m, lo, hi, st, R));
+    int rc_run = hsk_run_count(c, (const char*)d_reads.p, (const uint64_t*)d_offsets.p, n_reads, n_bases, k, m,
+                               lo, hi, st, R, pp);
+    if (pp) {
+        // every chunk copy is issued (an early error return may have left some)
+        // and finished before the buffers can be reused
+        for (; pipe.issued < pipe.n; ++pipe.issued) CK(pipe.issue(pipe.issued));
+        CK(cudaStreamSynchronize(c->cstream));
+    }
+    TRY(rc_run);
     size_t kb = (size_t)R.key_words * 8;
     HR.kmers.resize(R.n_pairs * R.key_words);
     HR.counts.resize(R.n_pairs);
@@ -1014,7 +1076,7 @@ extern "C" int hsk_stage_windows(hsk_ctx* c, const char* d_reads, const uint64_t
     c->zst = st;
     CK(cudaMemsetAsync(c->small, 0, 64, st));
     Encoded E;
-    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
+    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, false));
     SmParams P;
     fill_sm_params(c, E, k, m, 1, P);
     uint64_t warp_tiles = (n_bases + 1023) / 1024;
@@ -1044,9 +1106,9 @@ extern "C" int hsk_stage_supermers(hsk_ctx* c, const char* d_reads, const uint64
     CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
     c->ctr_used = 0;
     Encoded E;
-    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st));
+    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, false));
     Supermers S;
-    TRY(hsk_supermers(c, E, k, m, n_buckets, S, st));
+    TRY(hsk_supermers(c, E, k, m, n_buckets, S, st, nullptr));
     CK(cudaMemcpyAsync(d_bucket_kmers, c->bucket_kmers.p, (size_t)n_buckets * 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d_bucket_rec, c->bucket_rec.p, ((size_t)n_buckets + 1) * 8, cudaMemcpyDeviceToDevice, st));
     *d_records = S.records;

@@ -90,10 +90,31 @@ struct HostResult {
 
 struct ServeState;  // served form (hsk_serve.cu)
 
+// Input copied to the device in chunks on a copy stream while S1/S2 run on
+// the chunks already there (host-input counting).  issue(i) enqueues chunk
+// i's copy and records ev[i]; chunk bounds are multiples of 65536 bases.
+#define HSK_MAX_PIPE 8
+struct InputPipe {
+    int n = 0, issued = 0;
+    uint64_t bound[HSK_MAX_PIPE + 1] = {0};
+    cudaEvent_t ev[HSK_MAX_PIPE] = {};
+    const char* h_reads = nullptr;
+    char* d_reads = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaError_t issue(int i) {
+        cudaError_t e = cudaMemcpyAsync(d_reads + bound[i], h_reads + bound[i], bound[i + 1] - bound[i],
+                                        cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i], cs);
+        return e;
+    }
+};
+
 struct hsk_ctx {
     hsk_config cfg{};
     int num_sms = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cstream = nullptr;  // input copies of host-input counting
+    cudaEvent_t pipe_ev[HSK_MAX_PIPE] = {};
     cudaStream_t zst = nullptr;  // stream of the call in progress (orders zero-fills)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err_msg;
@@ -168,7 +189,7 @@ void hsk_set_error(hsk_ctx* c, const char* fmt, ...);
 int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new);
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
-                  DevResult& R);
+                  DevResult& R, InputPipe* pipe = nullptr);
 int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, uint64_t n_reads,
                       int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st, DevBuf& d_reads,
                       DevBuf& d_offsets, HostResult& HR);

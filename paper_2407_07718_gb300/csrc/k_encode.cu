@@ -22,11 +22,10 @@ __device__ __forceinline__ void encode4(uint32_t x, uint32_t& code8, uint32_t& i
 
 __global__ void __launch_bounds__(256) k_encode(const char* __restrict__ reads, uint64_t n_bases,
                                                 u64* __restrict__ packed, u64* __restrict__ invalid,
-                                                uint64_t n_packed_words, uint64_t n_mask_words,
+                                                uint64_t n_packed_words, uint64_t t0, uint64_t t1,
                                                 bool aligned16) {
-    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint64_t n_mw = n_mask_words;
-    if (t >= n_mw) return;
+    uint64_t t = t0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= t1) return;
     uint64_t b0 = t * 64;
     uint32_t x[16];
     if (aligned16 && b0 + 64 <= n_bases) {
@@ -89,7 +88,17 @@ void launch_encode(const char* reads, uint64_t n_bases, uint64_t* packed, uint64
     count_launch();
     bool al = (reinterpret_cast<uintptr_t>(reads) & 15) == 0;
     k_encode<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        reads, n_bases, (u64*)packed, (u64*)invalid, n_packed_words, threads, al);
+        reads, n_bases, (u64*)packed, (u64*)invalid, n_packed_words, 0, threads, al);
+}
+
+void launch_encode_range(const char* reads, uint64_t n_bases, uint64_t b0, uint64_t b1, uint64_t* packed,
+                         uint64_t* invalid, uint64_t n_packed_words, cudaStream_t st) {
+    const uint64_t t0 = b0 / 64, t1 = (b1 + 63) / 64;
+    if (t1 <= t0) return;
+    count_launch();
+    bool al = (reinterpret_cast<uintptr_t>(reads) & 15) == 0;
+    k_encode<<<(unsigned)((t1 - t0 + 255) / 256), 256, 0, st>>>(reads, n_bases, (u64*)packed, (u64*)invalid,
+                                                                n_packed_words, t0, t1, al);
 }
 
 void launch_mark_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,

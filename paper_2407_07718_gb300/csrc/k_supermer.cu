@@ -36,6 +36,9 @@ constexpr int SM_PW = SM_TW / 32 + 6;     // packed words staged per warp (even)
 constexpr int SM_MW = SM_TW / 64 + 4;     // mask words staged per warp (even)
 constexpr int SM_DBUF = 128;              // descriptors buffered per warp
 constexpr int SM_VW = SM_TW / 64;         // valid-window words per warp
+static_assert(SM_TW == (int)SM_TILE_BASES, "tile size");
+static_assert(SM_PW * 32 <= (int)SM_TILE_REACH && SM_MW * 64 <= (int)SM_TILE_REACH,
+              "a tile's staged words must lie within its declared reach");
 
 size_t supermer_smem_bytes(int mode, uint32_t n_buckets) {
     size_t s = (size_t)SM_WARPS * (SM_PW + 2 * SM_MW + SM_VW) * sizeof(u64);
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
     u64* wval = s_val + warp * SM_VW;
     u64* wdesc = s_desc + warp * SM_DBUF;
     int nbuf = 0;  // descriptors buffered by this warp (warp-uniform)
-    const u64 n_tiles = (P.n_bases + SM_TW - 1) / SM_TW;
+    const u64 n_tiles = P.tile_end ? P.tile_end : (P.n_bases + SM_TW - 1) / SM_TW;
 
     // append the buffered descriptors to the global list (one atomic per flush)
     auto flush = [&]() {
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
         nbuf = 0;
     };
 
-    for (u64 t = (u64)blockIdx.x * SM_WARPS + warp; t < n_tiles; t += (u64)gridDim.x * SM_WARPS) {
+    for (u64 t = P.tile_begin + (u64)blockIdx.x * SM_WARPS + warp; t < n_tiles; t += (u64)gridDim.x * SM_WARPS) {
         const u64 p0 = t * SM_TW;
         // ---- stage packed bases and masks (128-bit loads; p0 is 1024-aligned)
         {

@@ -187,3 +187,19 @@ def test_on_chip_and_global_paths_agree(hsk, tiny, case):
             assert a.last_overflow() > 0  # the global fallback ran next to the on-chip passes
     assert_same_result(ga, want, f"{case} on-chip")
     assert_same_result(gb, want, f"{case} global")
+
+
+def test_host_input_in_chunks_matches_device_input(hsk):
+    """Inputs of 64 MB or more reach the device in chunks while S1/S2 run on
+    the chunks already there; the result is the same as from device input."""
+    import torch
+    rs = datagen.long_read(scale=0.1)  # 150 Mbp
+    assert rs.n_bases >= (64 << 20)
+    with hsk.Context() as ctx:
+        got = ctx.count(rs.reads, rs.offsets, rs.k, rs.m, rs.lo, rs.hi)
+        r = ctx.count_device(dev(rs.reads), dev_u64(rs.offsets), rs.k, rs.m, rs.lo, rs.hi)
+        want = ctx.result_to_host(r)
+        again = ctx.count(rs.reads, rs.offsets, rs.k, rs.m, rs.lo, rs.hi)
+    assert_same_result(got, want, "chunked host input")
+    assert_same_result(again, want, "chunked host input, second call")
+    assert got.n_windows == oracle.n_windows(rs.reads, rs.offsets, rs.k)
