@@ -1,21 +1,26 @@
 // hsk_runtime.cu -- host runtime and C ABI of the k-mer counter.
 //
 // The context owns a device arena (named buffers grown on demand, all counted
-// against an HBM budget), a stream, a device error word and the look-back
-// bookkeeping (epoch-tagged status words, tile counters).  hsk_count_device
-// runs the whole pipeline on one stream:
+// against an HBM budget), a compute stream and a copy stream, a device error
+// word and the look-back bookkeeping (epoch-tagged status words, tile
+// counters).  hsk_count_device runs the whole pipeline on one stream:
 //
-//   S1 encode -> S2/S3 count supermers per (bucket, CTA) -> scan -> plan
-//   chunks of buckets under the budget -> S3 scatter records -> per chunk:
-//   S4 expand records to keys (+ digit histograms), 8-bit LSD passes ->
-//   S5 run heads, counts, histogram, filter -> S6 order pairs when the job
-//   took more than one chunk.
+//   S1 encode -> S2 supermer walk (descriptors, per-bucket counts) -> scan
+//   -> S3 scatter records into buckets -> plan chunks of buckets under the
+//   budget -> per chunk: group buckets, S4 count + scatter keys into
+//   (group, top digit) sub-segments, S4/S5 sort and count each sub-segment
+//   on chip (k_local.cu; the ones that do not fit go through the 8-bit LSD
+//   passes of k_sort.cu and the run scan of k_rle.cu) -> S6 order the kept
+//   pairs.  With local_sort = 0 every chunk takes the LSD passes and the run
+//   scan.  hsk_count copies large inputs in chunks on the copy stream while
+//   S1/S2 run on the chunks already there.
 //
 // Buckets are the paper's tasks (Sec. 3.4): a k-mer value never lands in two
-// of them, so chunks of buckets are sorted and counted independently, the way
-// the paper's workers count tasks.  The chunk planner plays the role of the
-// paper's memory-aware choice between an out-of-place and an in-place sort
-// (Sec. 3.1): it sizes each chunk so the out-of-place sort fits the budget.
+// of them, so chunks and groups of buckets are sorted and counted
+// independently, the way the paper's workers count tasks.  The chunk planner
+// plays the role of the paper's memory-aware choice between an out-of-place
+// and an in-place sort (Sec. 3.1): it sizes each chunk so its buffers fit the
+// budget.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

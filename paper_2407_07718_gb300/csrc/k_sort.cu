@@ -7,6 +7,10 @@
 // the tile's global digit offsets by decoupled look-back over earlier tiles
 // and scatters the tile, digit by digit, with contiguous writes.
 //
+// This is the global path: it sorts the sub-segments that do not fit the
+// on-chip sort (k_local.cu), the whole job when local_sort is off, the keys
+// of hsk_stage_sort / hsk_sort_keys_noalloc, and the output pairs (S6).
+//
 // Segments.  The keys of a job are split into C segments, each a group of
 // minimizer buckets -- the paper's tasks (Sec. 3.4), which never share a
 // k-mer value -- and every segment is sorted on its own, as the paper's
