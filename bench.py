@@ -52,7 +52,7 @@ UNIT = "k-mers/s"
 NCU_PER_KEY = {
     # long-read workload, k=31: k_local_sort passes 0 + 1, smsp__inst_executed.sum at full
     # size (1.4955 G keys); DRAM bytes from the 0.1-scale case (149.6 M keys), per key
-    ("long_read", "8fca31599648b42d"): {"inst": 11.7591, "dram": 8.3595},
+    ("long_read", "80cb490edf775baf"): {"inst": 11.5842, "dram": 8.3630},
 }
 # Issue slots of one GB300: 152 SMs x 4 warp schedulers x 1 warp instruction
 # per cycle (times the SM clock sampled during the run).
