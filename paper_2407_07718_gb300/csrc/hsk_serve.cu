@@ -11,6 +11,7 @@
 // Batched form: hsk_count_batch queues many independent read sets on the same
 // slots, largest first, and returns when all are done.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cstring>
 
@@ -145,7 +146,12 @@ static int serve_start(hsk_ctx* c) {
     if (c->serve) return HSK_OK;
     ServeState* S = new ServeState();
     S->budget = c->budget > c->allocated ? c->budget - c->allocated : 0;
+    // slots (child contexts running jobs side by side); HSK_SERVE_SLOTS overrides
     int n_slots = 4;
+    if (const char* e = getenv("HSK_SERVE_SLOTS")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 32) n_slots = v;
+    }
     for (int i = 0; i < n_slots; ++i) {
         hsk_config cfg = c->cfg;
         cfg.hbm_budget = S->budget;
