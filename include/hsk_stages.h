@@ -120,6 +120,12 @@ uint64_t hsk_debug_allocated(hsk_ctx* ctx);
 /* Keys of the context's last counting call that did not fit the on-chip
  * sort and went through the global radix passes instead (0 when none). */
 uint64_t hsk_debug_last_overflow(hsk_ctx* ctx);
+/* Failure detection without a GPU fault: runs the decoupled look-back wait
+ * that the scans and radix passes use, on a predecessor status word that
+ * nothing ever publishes, giving up after spin_limit polls (1 .. 2^24).
+ * Returns HSK_ETIMEOUT once the wait has given up and the kernel returned;
+ * the context stays usable. */
+int hsk_debug_wait_timeout(hsk_ctx* ctx, uint32_t spin_limit);
 
 /* Profiling hooks.  When enabled, each counting call on the context records
  * CUDA events on its own stream at the boundaries of its stages and adds the

@@ -94,6 +94,7 @@ def load():
             "hsk_debug_fail_alloc_after": ([P, i32], i32),
             "hsk_debug_allocated": ([P], u64),
             "hsk_debug_last_overflow": ([P], u64),
+            "hsk_debug_wait_timeout": ([P, u32], C.c_int),
             "hsk_profile_enable": ([P, i32], i32),
             "hsk_profile_read": ([P, C.POINTER(d), C.POINTER(u64), i32], i32),
             "hsk_launch_count": ([], u64),
@@ -365,6 +366,11 @@ class Context:
 
     def allocated(self) -> int:
         return int(self.lib.hsk_debug_allocated(self.h))
+
+    def wait_timeout(self, spin_limit: int) -> int:
+        """Run a bounded device wait on a flag nothing sets; returns the code
+        (HSK_ETIMEOUT expected).  See hsk_debug_wait_timeout."""
+        return int(self.lib.hsk_debug_wait_timeout(self.h, spin_limit))
 
     def last_overflow(self) -> int:
         """Keys of the last call that went through the global radix passes

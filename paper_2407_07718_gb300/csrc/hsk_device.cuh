@@ -149,7 +149,8 @@ __device__ __forceinline__ u64 lb_word(u64 flag, uint32_t epoch, u64 value) {
 // LB_SPIN_LIMIT empty reads the wait gives up, raises HSK_DERR_TIMEOUT and
 // returns what it has (the host then discards the result).
 __device__ __forceinline__ u64 lookback_exclusive(u64* status, u64 stride, u64 tile,
-                                                  uint32_t epoch, int* err) {
+                                                  uint32_t epoch, int* err,
+                                                  uint32_t spin_limit = HSK_SPIN_LIMIT) {
     u64 excl = 0;
     long long j = (long long)tile - 1;
     uint32_t spins = 0;
@@ -158,7 +159,7 @@ __device__ __forceinline__ u64 lookback_exclusive(u64* status, u64 stride, u64 t
         uint32_t ep = (uint32_t)(s >> 48) & 0x3FFF;
         u64 fl = s & (3ULL << 62);
         if (fl == 0 || ep != (epoch & 0x3FFF)) {
-            if (++spins > HSK_SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 raise_error(err, HSK_DERR_TIMEOUT);
                 break;
             }

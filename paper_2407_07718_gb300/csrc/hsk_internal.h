@@ -94,6 +94,11 @@ void launch_digit_offsets_seg(const uint64_t* hist, const uint64_t* key_base, ui
 // One LSD pass over C segments (tmax = most tiles of any segment), optionally
 // carrying uint32 values; status: C * tmax * 256 words; doff: this pass's [C][256].
 uint64_t onesweep_tile_keys(int key_words);
+// S6: counts into / out of the keys' bits from cshift up (cshift = 8 * passes)
+void launch_pack_pairs(void* keys, uint32_t* counts, uint64_t n, int key_words, int cshift, bool unpack, int grid,
+                       cudaStream_t st);
+// status: >= 2 * LB_PAD zeroed words
+void launch_debug_wait(uint64_t* status, uint32_t spin_limit, int* err, cudaStream_t st);
 void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
                          const uint64_t* key_base, uint32_t C, uint32_t tmax, int key_words, int shift,
                          const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err,

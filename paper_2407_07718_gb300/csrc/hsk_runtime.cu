@@ -174,6 +174,7 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
         return HSK_ECUDA;
     }
     c->budget = cfg.hbm_budget ? cfg.hbm_budget : (size_t)(free_b * 0.9);
+    c->host_res.set_pinned(true);  // hsk_count's results: reused from call to call
     c->allocated = HSK_SMALL_BYTES;
     char* s = (char*)c->small;
     c->d_err = (int*)(s + 0);
@@ -219,6 +220,7 @@ extern "C" int hsk_debug_fail_alloc_after(hsk_ctx* c, int n) {
 
 extern "C" uint64_t hsk_debug_allocated(hsk_ctx* c) { return c ? c->allocated : 0; }
 extern "C" uint64_t hsk_debug_last_overflow(hsk_ctx* c) { return c ? c->last_ov_keys : 0; }
+
 
 // ---------------------------------------------------------------------------
 // launch counter and stage profiling
@@ -625,8 +627,20 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
 
 // Order the output pairs by key (stage S6): segments and chunks are groups
 // of minimizer buckets, so their pairs come out in bucket order.
+// When every count is at most count_max (> 0) and fits the key bits above the
+// sort's top digit, the counts ride in those bits and the pairs are sorted as
+// keys alone; otherwise the counts move as values.
 int hsk_order_pairs(hsk_ctx* c, void* keys, uint32_t* counts, uint64_t n, int key_words,
-                    int key_bits, cudaStream_t st) {
+                    int key_bits, cudaStream_t st, uint32_t count_max) {
+    const int cshift = 8 * ((key_bits + 7) / 8);
+    const int spare = 64 * key_words - cshift;
+    if (n > 1 && count_max > 0 && spare > 0 && spare < 64 && (uint64_t)count_max < (1ULL << spare)) {
+        launch_pack_pairs(keys, counts, n, key_words, cshift, false, c->num_sms * 8, st);
+        TRY(plain_sort(c, keys, nullptr, n, key_words, key_bits, c->pair_alt_keys, nullptr, st));
+        launch_pack_pairs(keys, counts, n, key_words, cshift, true, c->num_sms * 8, st);
+        CK(cudaGetLastError());
+        return HSK_OK;
+    }
     return plain_sort(c, keys, counts, n, key_words, key_bits, c->pair_alt_keys, &c->pair_alt_counts, st);
 }
 
@@ -895,7 +909,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
         prof_mark(c, st, 5);
     }
     if (total_segments > 1 || unordered)
-        TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st));
+        TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st, hi));
     prof_mark(c, st, 6);
     CK(cudaEventRecord(c->ev1, st));
     uint32_t mx = 0;
@@ -1182,6 +1196,22 @@ extern "C" int hsk_stage_order(hsk_ctx* c, uint64_t* d_keys, uint32_t* d_counts,
     CK(cudaMemsetAsync(c->small, 0, 64, st));
     CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
     c->ctr_used = 0;
-    TRY(hsk_order_pairs(c, d_keys, d_counts, n, key_words, key_bits, st));
+    TRY(hsk_order_pairs(c, d_keys, d_counts, n, key_words, key_bits, st, 0));
     return read_device_error(c, st);
+}
+
+extern "C" int hsk_debug_wait_timeout(hsk_ctx* c, uint32_t spin_limit) {
+    if (!c || spin_limit < 1 || spin_limit > HSK_SPIN_LIMIT) return HSK_EINVAL;
+    CK(cudaSetDevice(c->cfg.device));
+    cudaStream_t st = c->stream;
+    c->zst = st;
+    TRY(hsk_ensure(c, c->batch_c, 256, false));  // two padded status words
+    CK(cudaMemsetAsync(c->batch_c.p, 0, 256, st));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    launch_debug_wait((uint64_t*)c->batch_c.p, spin_limit, c->d_err, st);
+    CK(cudaGetLastError());
+    const int rc = read_device_error(c, st);
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return rc;
 }

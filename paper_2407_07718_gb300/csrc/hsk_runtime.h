@@ -65,19 +65,61 @@ struct DevResult {
 
 // Host array whose elements are left uninitialised on resize: a device copy
 // fills them at once, so zero-filling hundreds of MB first would be wasted.
+// A pinned array (page-locked, grown only) takes device copies at link speed
+// and keeps its pages from call to call; if pinning fails it falls back to
+// ordinary memory.
 template <class T>
 struct HostArr {
-    std::unique_ptr<T[]> p;
+    T* p = nullptr;
     size_t n = 0, cap = 0;
+    bool pinned = false, is_pinned = false;
+    HostArr() = default;
+    HostArr(const HostArr&) = delete;
+    HostArr& operator=(const HostArr&) = delete;
+    HostArr(HostArr&& o) noexcept { take(o); }
+    HostArr& operator=(HostArr&& o) noexcept {
+        if (this != &o) {
+            release();
+            take(o);
+        }
+        return *this;
+    }
+    ~HostArr() { release(); }
+    void take(HostArr& o) {
+        p = o.p;
+        n = o.n;
+        cap = o.cap;
+        pinned = o.pinned;
+        is_pinned = o.is_pinned;
+        o.p = nullptr;
+        o.n = o.cap = 0;
+    }
+    void release() {
+        if (p) {
+            if (is_pinned) cudaFreeHost(p);
+            else delete[] p;
+        }
+        p = nullptr;
+        cap = 0;
+        is_pinned = false;
+    }
     void resize(size_t m) {
         if (m > cap) {
-            p.reset(new T[m]);
+            release();
+            void* q = nullptr;
+            if (pinned && cudaMallocHost(&q, m * sizeof(T)) == cudaSuccess) {
+                p = static_cast<T*>(q);
+                is_pinned = true;
+            } else {
+                cudaGetLastError();  // a failed pin is not an error of the call
+                p = new T[m];
+            }
             cap = m;
         }
         n = m;
     }
-    T* data() { return p.get(); }
-    const T* data() const { return p.get(); }
+    T* data() { return p; }
+    const T* data() const { return p; }
     size_t size() const { return n; }
 };
 
@@ -86,6 +128,7 @@ struct HostResult {
     HostArr<uint64_t> kmers;
     HostArr<uint32_t> counts;
     HostArr<uint64_t> hist;
+    void set_pinned(bool on) { kmers.pinned = counts.pinned = hist.pinned = on; }
 };
 
 struct ServeState;  // served form (hsk_serve.cu)

@@ -618,6 +618,13 @@ void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint3
                          cudaStream_t st) {
     if (C == 0 || tmax == 0) return;
     bool hv = vin != nullptr;
+    if (!hv && key_words == 2) {
+        // 128-bit keys alone: the tile-per-CTA pass (the persistent TMA pass
+        // below measured slower for them: 1.5 against 2.7 TB/s)
+        launch_pass_t<key128, false>(kin, kout, nullptr, nullptr, key_base, C, tmax, shift, doff, status, tile_ctr,
+                                     epoch, err, st);
+        return;
+    }
     if (!hv) {  // persistent, TMA-staged pass
         static int num_sms = 0;
         if (!num_sms) {
@@ -645,6 +652,66 @@ void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint3
     }
     if (key_words == 1) launch_pass_t<u64, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
     else launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
+}
+
+// ---------------------------------------------------------------------------
+// S6 with the counts carried in the keys' spare bits
+// ---------------------------------------------------------------------------
+// A key of 2k bits sorted on its ceil(2k/8) 8-bit digits leaves the bits from
+// cshift = 8 * ceil(2k/8) up unexamined by every pass; when the counts fit
+// there, the pairs are sorted as keys alone (key-only passes move 8 * words
+// bytes per element instead of 8 * words + 4).
+template <typename K>
+__global__ void __launch_bounds__(256) k_pack_pairs(K* keys, const uint32_t* __restrict__ counts, u64 n, int cshift) {
+    for (u64 i = (u64)blockIdx.x * 256 + threadIdx.x; i < n; i += (u64)gridDim.x * 256) {
+        if constexpr (std::is_same<K, u64>::value) keys[i] |= (u64)counts[i] << cshift;
+        else keys[i].hi |= (u64)counts[i] << (cshift - 64);
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_unpack_pairs(K* keys, uint32_t* __restrict__ counts, u64 n, int cshift) {
+    for (u64 i = (u64)blockIdx.x * 256 + threadIdx.x; i < n; i += (u64)gridDim.x * 256) {
+        if constexpr (std::is_same<K, u64>::value) {
+            const u64 v = keys[i];
+            counts[i] = (uint32_t)(v >> cshift);
+            keys[i] = v & ((1ULL << cshift) - 1);
+        } else {
+            const u64 h = keys[i].hi;
+            const int s = cshift - 64;
+            counts[i] = (uint32_t)(h >> s);
+            keys[i].hi = s == 0 ? 0ULL : (h & ((1ULL << s) - 1));
+        }
+    }
+}
+
+void launch_pack_pairs(void* keys, uint32_t* counts, uint64_t n, int key_words, int cshift, bool unpack, int grid,
+                       cudaStream_t st) {
+    if (n == 0) return;
+    count_launch();
+    const uint64_t need = (n + 255) / 256;
+    const unsigned g = (unsigned)(need < (uint64_t)grid ? need : (uint64_t)grid);
+    if (key_words == 1) {
+        if (unpack) k_unpack_pairs<u64><<<g, 256, 0, st>>>((u64*)keys, counts, n, cshift);
+        else k_pack_pairs<u64><<<g, 256, 0, st>>>((u64*)keys, counts, n, cshift);
+    } else {
+        if (unpack) k_unpack_pairs<key128><<<g, 256, 0, st>>>((key128*)keys, counts, n, cshift);
+        else k_pack_pairs<key128><<<g, 256, 0, st>>>((key128*)keys, counts, n, cshift);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// failure detection: the look-back wait on a word nothing publishes
+// ---------------------------------------------------------------------------
+// Tile 1 waits for tile 0's status word, which stays zero: the wait gives up
+// after spin_limit polls, records HSK_DERR_TIMEOUT and the kernel returns.
+__global__ void k_debug_wait(u64* status, uint32_t spin_limit, int* err) {
+    if (threadIdx.x == 0) (void)lookback_exclusive(status, LB_PAD, 1, 1, err, spin_limit);
+}
+
+void launch_debug_wait(uint64_t* status, uint32_t spin_limit, int* err, cudaStream_t st) {
+    count_launch();
+    k_debug_wait<<<1, 32, 0, st>>>((u64*)status, spin_limit, err);
 }
 
 }  // namespace hsk

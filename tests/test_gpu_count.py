@@ -203,3 +203,17 @@ def test_host_input_in_chunks_matches_device_input(hsk):
     assert_same_result(got, want, "chunked host input")
     assert_same_result(again, want, "chunked host input, second call")
     assert got.n_windows == oracle.n_windows(rs.reads, rs.offsets, rs.k)
+
+
+@pytest.mark.parametrize("limit", [1, 1000, 50_000])
+def test_bounded_wait_gives_up_and_context_stays_usable(hsk, tiny, limit):
+    """A look-back wait on a status word nothing publishes gives up after its
+    spin limit: the kernel returns, the host reads HSK_ETIMEOUT, and the same
+    context then counts correctly (no GPU fault, no hang)."""
+    n = 2000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    want = oracle.count(reads, offs, 31, 2, 1000)
+    with hsk.Context() as ctx:
+        assert ctx.wait_timeout(limit) == -4  # HSK_ETIMEOUT
+        assert_same_result(ctx.count(reads, offs, 31, 17, 2, 1000), want, "after a timed-out wait")
+        assert ctx.wait_timeout(limit) == -4
