@@ -364,13 +364,14 @@ def main():
         if rank != 0:
             return
         steps = max(1, args.steps)
-        nw, times, nreads = run_cpu_oracle(rs, args.cpu_windows, steps=1)
-        # the oracle's time is steady: one timed sample per requested step would
-        # take minutes, so the steps after the first reuse its measured rate
-        tot = times[0] * steps
+        # each step counts the same bounded sample (the first reads holding
+        # about --cpu-windows windows); warm-up steps are not timed
+        run_cpu_oracle(rs, args.cpu_windows, steps=args.warmup)
+        nw, times, nreads = run_cpu_oracle(rs, args.cpu_windows, steps=steps)
+        tot = sum(times)
         value = nw * steps / tot
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-                "steps": steps, "warmup": 0, "ms_per_step": times[0] * 1e3, "higher_is_better": True,
+                "steps": steps, "warmup": args.warmup, "ms_per_step": tot / steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64" if kw == 1 else "u128",
                 "data": "synthetic", "config": config,
                 "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
