@@ -480,6 +480,10 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
     constexpr int PF = BIG ? 0 : CAP / NT;
     constexpr int PFN = PF > 0 ? PF : 1;
     K pf[PFN];
+    // the first partition's counters start at zero; each sub-segment clears
+    // them again after its last barrier, ready for the next one
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) s_cnt1[tid * BPT + j] = 0;
     if (tid == 0) s_next = atomicAdd(claim, 1u);
     __syncthreads();
     uint32_t si = s_next;
@@ -521,9 +525,6 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
             continue;
         }
         // ---- first partition: load + count, scan, scatter A -> B
-#pragma unroll
-        for (int j = 0; j < BPT; ++j) s_cnt1[tid * BPT + j] = 0;
-        __syncthreads();
         if (PF > 0) {
 #pragma unroll
             for (int j = 0; j < PFN; ++j) {
@@ -549,8 +550,13 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
             bc[j] = s_cnt1[tid * BPT + j];
             sum += bc[j];
         }
-        uint32_t tot;
-        const uint32_t my0 = block_excl_sum<NT, uint32_t>(sum, s_scr32, tot);
+        // exclusive prefix of the per-thread sums: warp scan, then every warp
+        // adds the totals of the warps before it (one barrier)
+        const uint32_t winc = warp_incl_sum<uint32_t>(sum);
+        if (lane == 31) s_scr32[warp] = winc;
+        __syncthreads();
+        uint32_t my0 = winc - sum;
+        for (int w = 0; w < warp; ++w) my0 += s_scr32[w];
         {
             uint32_t run = my0;
 #pragma unroll
@@ -726,6 +732,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
         // s_abort: an impossible bin was met (raise_error has been called)
         __syncthreads();
         if (tid == 0) kc[s] = s_kept;
+#pragma unroll
+        for (int j = 0; j < BPT; ++j) s_cnt1[tid * BPT + j] = 0;
         si = nxt;
     }
     if (my_ones) atomicAdd(&s_hist[1], my_ones);  // hist_len >= 2: count 1 has its own bin
