@@ -729,8 +729,11 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                                      bin.shift == 0, bin.buf ^ 1, s_stack, &s_sp, &s_abort, err, emit);
             __syncthreads();
         }
-        // s_abort: an impossible bin was met (raise_error has been called)
-        __syncthreads();
+        // The partition loop exits on a check made right after a barrier (the
+        // one after the larger bins, or its own last one), so every run has
+        // been emitted and the counters are no longer read: no barrier needed
+        // before the kept count is stored and the counters cleared.
+        // (s_abort: an impossible bin was met; raise_error has been called.)
         if (tid == 0) kc[s] = s_kept;
 #pragma unroll
         for (int j = 0; j < BPT; ++j) s_cnt1[tid * BPT + j] = 0;
