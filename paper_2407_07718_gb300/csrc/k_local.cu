@@ -136,12 +136,14 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
             }
             T = run;
         }
+        // Four barriers a round.  A thread clears its digit counter as soon as
+        // it has read it, and the round's write-out needs no barrier after it:
+        // the next round writes only s_raw and s_cnt before its first barrier.
         K* out = reinterpret_cast<K*>(keys_out);
+        const int lane = tid & 31, warp = tid >> 5;
         for (uint32_t j0 = 0; j0 < T; j0 += ROUND) {
             const uint32_t nround = T - j0 < (uint32_t)ROUND ? T - j0 : (uint32_t)ROUND;
-            s_cnt[tid] = 0;
-            __syncthreads();
-            // keys of this round into s_keys (tile order), digits counted
+            // keys of this round into s_raw (tile order), digits counted
 #pragma unroll
             for (int i = 0; i < EXP_RPT; ++i) {
                 if (pre[i] + nk[i] > j0 && pre[i] < j0 + nround)
@@ -155,8 +157,12 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
             }
             __syncthreads();
             const uint32_t cnt = s_cnt[tid];
-            uint32_t tot;
-            const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(cnt, s_scr32, tot);
+            s_cnt[tid] = 0;
+            const uint32_t winc = warp_incl_sum<uint32_t>(cnt);
+            if (lane == 31) s_scr32[warp] = winc;
+            __syncthreads();
+            uint32_t ex = winc - cnt;
+            for (int w = 0; w < warp; ++w) ex += s_scr32[w];
             s_dstart[tid] = ex;
             s_fill[tid] = ex;
             if (cnt) {
@@ -180,7 +186,6 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
                 const u64 at = s_gbase[d];
                 if (at != ~0ULL) out[at + (i - s_dstart[d])] = key;
             }
-            __syncthreads();
         }
     }
 }
