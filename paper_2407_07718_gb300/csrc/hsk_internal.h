@@ -62,7 +62,12 @@ struct SmParams {
 size_t supermer_smem_bytes(int mode, uint32_t n_buckets);
 int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets);
 void launch_supermer(int mode, const SmParams& p, cudaStream_t st);
-// records from descriptors: bucket_off[B+1] record offsets, cursor[B] zeroed
+// records from descriptors: bucket_off[B+1] record offsets; cursor[b *
+// SCATTER_CURSOR_STRIDE] zeroed for every bucket b.  The cursors take every
+// descriptor's atomic: packed into 16 KB they fell into a few L2 slices, and
+// 128 bytes apart they spread over all of them (S3 took 6.2 ms packed, 5.35 ms
+// spread, on the long-read workload)
+constexpr uint32_t SCATTER_CURSOR_STRIDE = 32;
 void launch_scatter_desc(const uint64_t* desc, uint64_t n_desc, const uint64_t* packed, int k,
                          const uint64_t* bucket_off, uint32_t* cursor, uint64_t* records, uint64_t n_records,
                          int* err, int grid, cudaStream_t st);

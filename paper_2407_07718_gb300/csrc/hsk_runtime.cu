@@ -394,7 +394,9 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
     P.grid = (uint32_t)std::max<uint64_t>(g, 1);
     TRY(hsk_ensure(c, c->bucket_kmers, (uint64_t)B * 8, false));
     TRY(hsk_ensure(c, c->bucket_rec, ((uint64_t)B + 1) * 8, false));
-    TRY(hsk_ensure(c, c->cta_cnt, (uint64_t)B * 4 * 2, false));  // records per bucket, then cursors
+    // records per bucket, then the bucket cursors of the scatter (spread out)
+    const size_t cnt_bytes = (size_t)B * 4 * (1 + SCATTER_CURSOR_STRIDE);
+    TRY(hsk_ensure(c, c->cta_cnt, cnt_bytes, false));
     uint32_t* d_rec_cnt = (uint32_t*)c->cta_cnt.p;
     uint32_t* d_cursor = d_rec_cnt + B;
     // descriptors: about 2/(w+1) supermers per window (random minimizers), plus
@@ -405,7 +407,7 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
     for (int attempt = 0; attempt < 2; ++attempt) {
         TRY(hsk_ensure(c, c->cta_off, cap * 8, false));
         CK(cudaMemsetAsync(c->bucket_kmers.p, 0, (size_t)B * 8, st));
-        CK(cudaMemsetAsync(d_rec_cnt, 0, (size_t)B * 4 * 2, st));
+        CK(cudaMemsetAsync(d_rec_cnt, 0, cnt_bytes, st));
         CK(cudaMemsetAsync(c->d_ndesc, 0, 8, st));
         P.desc = (uint64_t*)c->cta_off.p;
         P.desc_cap = cap;

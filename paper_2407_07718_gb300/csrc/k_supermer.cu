@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) k_scatter_desc(const u64* __restrict__ de
         const u64 d = desc[i];
         const u64 pos = d & ((1ULL << 40) - 1);
         const uint32_t n = (uint32_t)(d >> 40) & 0xFF, b = (uint32_t)(d >> 48);
-        const u64 slot = bucket_off[b] + atomicAdd(cursor + b, 1u);
+        const u64 slot = bucket_off[b] + atomicAdd(cursor + (size_t)b * SCATTER_CURSOR_STRIDE, 1u);
         if (slot >= n_records || slot >= bucket_off[b + 1]) {
             raise_error(err, HSK_DERR_BOUNDS);
             continue;
