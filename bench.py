@@ -52,7 +52,7 @@ UNIT = "k-mers/s"
 NCU_PER_KEY = {
     # long-read workload, k=31: k_local_sort passes 0 + 1, smsp__inst_executed.sum at full
     # size (1.4955 G keys); DRAM bytes from the 0.1-scale case (149.6 M keys), per key
-    ("long_read", "c84692105c73842f"): {"inst": 11.5683, "dram": 8.3637},
+    ("long_read", "28196a6506179be2"): {"inst": 11.5679, "dram": 8.3418},
 }
 # Issue slots of one GB300: 152 SMs x 4 warp schedulers x 1 warp instruction
 # per cycle (times the SM clock sampled during the run).

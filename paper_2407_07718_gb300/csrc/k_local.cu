@@ -40,24 +40,82 @@ constexpr int LP_NT = 256;
 // ---------------------------------------------------------------------------
 template <bool WIDE>
 struct PartCfg {
-    static constexpr int ROUND = WIDE ? 2048 : 4096;  // keys grouped per scatter round
+    static constexpr int RW = WIDE ? 4 : 2;            // words per supermer record
+    static constexpr int ROUND = WIDE ? 2048 : 4096;   // keys grouped per scatter round
+    static constexpr int LR = ROUND / LP_NT;           // keys per thread and round
 };
+static_assert(EXP_TILE == 4 * LP_NT, "a thread sums the k-mer counts of four records");
 
+// Dynamic shared memory of MODE 1: [keys grouped by digit][records][count prefix][counts]
 size_t part_smem_bytes(int mode, int k) {
     if (mode == 0) return 0;
-    return 2 * (k > 32 ? (size_t)PartCfg<true>::ROUND * 16 : (size_t)PartCfg<false>::ROUND * 8);
+    const bool wide = k > 32;
+    return (size_t)EXP_TILE * (wide ? 4 : 2) * 8 + (size_t)(EXP_TILE + 4) * 4 + EXP_TILE +
+           (wide ? (size_t)PartCfg<true>::ROUND * 16 : (size_t)PartCfg<false>::ROUND * 8);
 }
 
+// Consecutive keys of a staged tile: key j is k-mer j - s_pre[r] of the
+// record r with s_pre[r] <= j < s_pre[r + 1].  Moving forward only reads the
+// next records' bounds, so a thread walking a run of keys finds its first
+// record by binary search and the others by stepping.
+template <bool WIDE>
+struct TileWalk {
+    using K = typename std::conditional<WIDE, key128, u64>::type;
+    const u64* s_rec;
+    const uint32_t* s_pre;
+    uint32_t r, rb, re;
+    u64 W[4];
+    __device__ __forceinline__ void load() {
+        constexpr int RW = PartCfg<WIDE>::RW;
+        W[0] = s_rec[r * RW];
+        W[1] = s_rec[r * RW + 1];
+        W[2] = WIDE ? s_rec[r * RW + 2] : 0ULL;
+        W[3] = WIDE ? s_rec[r * RW + 3] : 0ULL;
+    }
+    // start at key j < s_pre[nr] (the tile's key count)
+    __device__ __forceinline__ void seek(uint32_t nr, uint32_t j) {
+        uint32_t lo = 0, hi = nr;  // s_pre[lo] <= j < s_pre[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_pre[mid] <= j) lo = mid;
+            else hi = mid;
+        }
+        r = lo;
+        rb = s_pre[lo];
+        re = s_pre[lo + 1];
+        load();
+    }
+    // canonical key j (j at or after the last key asked for, j < the tile's key count)
+    __device__ __forceinline__ K key(uint32_t j, int k) {
+        if (j >= re) {
+            do {
+                ++r;
+                rb = re;
+                re = s_pre[r + 1];
+            } while (j >= re);
+            load();
+        }
+        if constexpr (WIDE) return canonical128(record_kmer128(W, j - rb, k), k);
+        else return canonical64(record_kmer64(W, j - rb, k), k);
+    }
+};
+
 // Work: one counter over all record tiles of all groups; tile g belongs to
-// group tile_seg[g] and is tile g - tile_base[group] of it.  Thread t holds
-// records t, t + 256, ... of the tile (EXP_RPT of them) and rolls through
-// their k-mers (record_kmers).
+// group tile_seg[g] and is tile g - tile_base[group] of it.
 // MODE 0: sub_cnt[c * 256 + d] += keys of group c whose digit at `shift` is d.
+//         Thread t holds records t, t + 256, ... of the tile (EXP_RPT of
+//         them) and rolls through their k-mers (record_kmers).
 // MODE 1: every key to keys_out[cursor[c * 256 + d]++] (a reservation per
-//         digit and round), never past sub_end[c * 256 + d].  A round takes
-//         the tile's keys [j0, j0 + ROUND) in record order: the records that
-//         reach into the window write their keys there, the round is grouped
-//         by digit in shared memory and written out as one run per digit.
+//         digit and round), never past sub_end[c * 256 + d].  The tile's
+//         records are staged in shared memory with the prefix of their k-mer
+//         counts; a round takes the tile's keys [j0, j0 + ROUND), LR
+//         consecutive keys per thread, cut out of their records (TileWalk)
+//         and held in registers, so every thread has the same number of keys
+//         whatever the records' lengths.  The round is grouped by digit in
+//         shared memory and written out as one run per digit.
+// (Rolling is cheaper per key than cutting each key out, but a thread per
+// record leaves lanes idle while the warp's longest record is expanded; in
+// the count pass that costs less than cutting, in the scatter pass more.)
 template <bool WIDE, int MODE>
 __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
                                                 const u64* __restrict__ tile_base, const uint32_t* __restrict__ tile_seg,
@@ -66,11 +124,14 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
                                                 const u64* __restrict__ sub_end, void* __restrict__ keys_out,
                                                 int* err) {
     using K = typename std::conditional<WIDE, key128, u64>::type;
-    constexpr int RW = WIDE ? 4 : 2;
+    constexpr int RW = PartCfg<WIDE>::RW;
     constexpr int ROUND = PartCfg<WIDE>::ROUND;
+    constexpr int LR = PartCfg<WIDE>::LR;
     extern __shared__ __align__(16) u64 smem_part[];
-    K* s_raw = reinterpret_cast<K*>(smem_part);  // a round's keys in tile order (MODE 1)
-    K* s_keys = s_raw + ROUND;                    // the same keys grouped by digit
+    K* s_keys = reinterpret_cast<K*>(smem_part);                    // MODE 1: a round grouped by digit
+    u64* s_rec = smem_part + (size_t)ROUND * RW / 2;                 // MODE 1: the tile's records
+    uint32_t* s_pre = reinterpret_cast<uint32_t*>(s_rec + (size_t)EXP_TILE * RW);  // [EXP_TILE + 1]
+    uint8_t* s_nk = reinterpret_cast<uint8_t*>(s_pre + EXP_TILE + 4);              // [EXP_TILE]
     __shared__ uint32_t s_cnt[256], s_fill[256], s_dstart[256];
     __shared__ u64 s_gbase[256];
     __shared__ uint32_t s_scr32[9];
@@ -89,28 +150,28 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
         const u64 r0 = tile * EXP_TILE;
         const uint32_t nr = (uint32_t)(n_rec - r0 < (u64)EXP_TILE ? n_rec - r0 : (u64)EXP_TILE);
         const u64* trec = rec + (rb + r0) * RW;
-        // this thread's records, in registers
-        u64 W[EXP_RPT][4];
-        uint32_t nk[EXP_RPT];
+        if constexpr (MODE == 0) {
+            // this thread's records, in registers
+            u64 W[EXP_RPT][4];
+            uint32_t nk[EXP_RPT];
 #pragma unroll
-        for (int i = 0; i < EXP_RPT; ++i) {
-            const uint32_t r = (uint32_t)i * LP_NT + tid;
-            nk[i] = 0;
-            W[i][0] = W[i][1] = W[i][2] = W[i][3] = 0;
-            if (r < nr) {
-                const ulonglong2* q = reinterpret_cast<const ulonglong2*>(trec + (u64)r * RW);
-                const ulonglong2 a = q[0];
-                W[i][0] = a.x;
-                W[i][1] = a.y;
-                if (WIDE) {
-                    const ulonglong2 b2 = q[1];
-                    W[i][2] = b2.x;
-                    W[i][3] = b2.y;
+            for (int i = 0; i < EXP_RPT; ++i) {
+                const uint32_t r = (uint32_t)i * LP_NT + tid;
+                nk[i] = 0;
+                W[i][0] = W[i][1] = W[i][2] = W[i][3] = 0;
+                if (r < nr) {
+                    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(trec + (u64)r * RW);
+                    const ulonglong2 a = q[0];
+                    W[i][0] = a.x;
+                    W[i][1] = a.y;
+                    if (WIDE) {
+                        const ulonglong2 b2 = q[1];
+                        W[i][2] = b2.x;
+                        W[i][3] = b2.y;
+                    }
+                    nk[i] = (uint32_t)(W[i][RW - 1] & 0xFF);
                 }
-                nk[i] = (uint32_t)(W[i][RW - 1] & 0xFF);
             }
-        }
-        if (MODE == 0) {
 #pragma unroll
             for (int i = 0; i < EXP_RPT; ++i)
                 record_kmers<WIDE>(W[i], nk[i], k,
@@ -119,72 +180,94 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
             const uint32_t v = s_cnt[tid];
             if (v) atomicAdd(sub_cnt + (u64)c * 256 + tid, v);
             s_cnt[tid] = 0;
-            continue;
-        }
-        // record r's keys are tile keys [pre[i], pre[i] + nk[i]); records are
-        // taken in the order i * 256 + tid, so the prefix runs over (i, tid)
-        uint32_t pre[EXP_RPT];
-        uint32_t T = 0;
-        {
-            uint32_t run = 0;
+        } else {
+            // ---- stage the records (128-bit loads) and their k-mer counts
+            {
+                const ulonglong2* src = reinterpret_cast<const ulonglong2*>(trec);
+                ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rec);
 #pragma unroll
-            for (int i = 0; i < EXP_RPT; ++i) {
-                uint32_t tot;
-                const uint32_t ex = block_excl_sum<LP_NT, uint32_t>(nk[i], s_scr32, tot);
-                pre[i] = run + ex;
-                run += tot;
-            }
-            T = run;
-        }
-        // Four barriers a round.  A thread clears its digit counter as soon as
-        // it has read it, and the round's write-out needs no barrier after it:
-        // the next round writes only s_raw and s_cnt before its first barrier.
-        K* out = reinterpret_cast<K*>(keys_out);
-        const int lane = tid & 31, warp = tid >> 5;
-        for (uint32_t j0 = 0; j0 < T; j0 += ROUND) {
-            const uint32_t nround = T - j0 < (uint32_t)ROUND ? T - j0 : (uint32_t)ROUND;
-            // keys of this round into s_raw (tile order), digits counted
-#pragma unroll
-            for (int i = 0; i < EXP_RPT; ++i) {
-                if (pre[i] + nk[i] > j0 && pre[i] < j0 + nround)
-                    record_kmers<WIDE>(W[i], nk[i], k, [&](uint32_t j, const K& key) {
-                        const uint32_t pos = pre[i] + j;
-                        if (pos >= j0 && pos < j0 + nround) {
-                            s_raw[pos - j0] = key;
-                            atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u);
+                for (int i = 0; i < EXP_RPT; ++i) {
+                    const uint32_t r = (uint32_t)i * LP_NT + tid;
+                    uint32_t n = 0;
+                    if (r < nr) {
+                        const ulonglong2 a = src[(size_t)r * (RW / 2)];
+                        dst[(size_t)r * (RW / 2)] = a;
+                        if (WIDE) {
+                            const ulonglong2 b = src[(size_t)r * (RW / 2) + 1];
+                            dst[(size_t)r * (RW / 2) + 1] = b;
+                            n = (uint32_t)(b.y & 0xFF);
+                        } else {
+                            n = (uint32_t)(a.y & 0xFF);
                         }
-                    });
-            }
-            __syncthreads();
-            const uint32_t cnt = s_cnt[tid];
-            s_cnt[tid] = 0;
-            const uint32_t winc = warp_incl_sum<uint32_t>(cnt);
-            if (lane == 31) s_scr32[warp] = winc;
-            __syncthreads();
-            uint32_t ex = winc - cnt;
-            for (int w = 0; w < warp; ++w) ex += s_scr32[w];
-            s_dstart[tid] = ex;
-            s_fill[tid] = ex;
-            if (cnt) {
-                const u64 slot = (u64)c * 256 + tid;
-                u64 at = atomicAdd(cursor + slot, (unsigned long long)cnt);
-                if (at + cnt > sub_end[slot]) {
-                    raise_error(err, HSK_DERR_BOUNDS);
-                    at = ~0ULL;
+                    }
+                    s_nk[r] = (uint8_t)n;
                 }
-                s_gbase[tid] = at;
             }
             __syncthreads();
-            for (uint32_t j = tid; j < nround; j += LP_NT) {  // group the round by digit
-                const K key = s_raw[j];
-                s_keys[atomicAdd(&s_fill[key_digit(key, shift, 0xFF)], 1u)] = key;
+            uint32_t T;
+            {
+                // records 4t .. 4t+3: their counts' exclusive prefix
+                const uint32_t q = reinterpret_cast<const uint32_t*>(s_nk)[tid];
+                const uint32_t n0 = q & 0xFF, n1 = (q >> 8) & 0xFF, n2 = (q >> 16) & 0xFF, n3 = q >> 24;
+                const uint32_t e = block_excl_sum<LP_NT, uint32_t>(n0 + n1 + n2 + n3, s_scr32, T);
+                reinterpret_cast<uint4*>(s_pre)[tid] = make_uint4(e, e + n0, e + n0 + n1, e + n0 + n1 + n2);
+                if (tid == 0) s_pre[EXP_TILE] = T;
             }
             __syncthreads();
-            for (uint32_t i = tid; i < nround; i += LP_NT) {
-                const K key = s_keys[i];
-                const uint32_t d = key_digit(key, shift, 0xFF);
-                const u64 at = s_gbase[d];
-                if (at != ~0ULL) out[at + (i - s_dstart[d])] = key;
+            TileWalk<WIDE> walk{s_rec, s_pre};
+            // Four barriers a round.  A thread clears its digit counter as soon
+            // as it has read it, and the round's write-out needs no barrier
+            // after it: the next round writes only registers and s_cnt before
+            // its first barrier, and the next tile's staging comes after the
+            // tile loop's barriers.
+            K* out = reinterpret_cast<K*>(keys_out);
+            const int lane = tid & 31, warp = tid >> 5;
+            for (uint32_t j0 = 0; j0 < T; j0 += ROUND) {
+                const uint32_t nround = T - j0 < (uint32_t)ROUND ? T - j0 : (uint32_t)ROUND;
+                // this thread's keys: [jb, je), at most LR of them
+                const uint32_t jb = j0 + (uint32_t)tid * LR;
+                const uint32_t je = jb + LR < j0 + nround ? jb + LR : j0 + nround;
+                K kr[LR];
+                if (jb < je) {
+                    walk.seek(nr, jb);
+#pragma unroll
+                    for (int i = 0; i < LR; ++i) {
+                        if (jb + i < je) {
+                            kr[i] = walk.key(jb + i, k);
+                            atomicAdd(&s_cnt[key_digit(kr[i], shift, 0xFF)], 1u);
+                        }
+                    }
+                }
+                __syncthreads();
+                const uint32_t cnt = s_cnt[tid];
+                s_cnt[tid] = 0;
+                const uint32_t winc = warp_incl_sum<uint32_t>(cnt);
+                if (lane == 31) s_scr32[warp] = winc;
+                __syncthreads();
+                uint32_t ex = winc - cnt;
+                for (int w = 0; w < warp; ++w) ex += s_scr32[w];
+                s_dstart[tid] = ex;
+                s_fill[tid] = ex;
+                if (cnt) {
+                    const u64 slot = (u64)c * 256 + tid;
+                    u64 at = atomicAdd(cursor + slot, (unsigned long long)cnt);
+                    if (at + cnt > sub_end[slot]) {
+                        raise_error(err, HSK_DERR_BOUNDS);
+                        at = ~0ULL;
+                    }
+                    s_gbase[tid] = at;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < LR; ++i)  // group the round by digit
+                    if (jb + i < je) s_keys[atomicAdd(&s_fill[key_digit(kr[i], shift, 0xFF)], 1u)] = kr[i];
+                __syncthreads();
+                for (uint32_t i = tid; i < nround; i += LP_NT) {
+                    const K key = s_keys[i];
+                    const uint32_t d = key_digit(key, shift, 0xFF);
+                    const u64 at = s_gbase[d];
+                    if (at != ~0ULL) out[at + (i - s_dstart[d])] = key;
+                }
             }
         }
     }
