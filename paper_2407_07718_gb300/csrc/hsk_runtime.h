@@ -63,16 +63,98 @@ struct DevResult {
     double device_ms;
 };
 
+// Host blocks for the results the batched and served forms hand out.  Each
+// job's arrays are filled by device copies and held by the caller until its
+// ticket is released (or the next batch); freshly allocated pageable memory
+// would be faulted in page by page during that copy, and a new pinned block
+// costs a slow pinning call, so released blocks are kept and reused by later
+// jobs.  Blocks are pinned up to PIN_CAP bytes in total, pageable beyond;
+// at most KEEP_CAP bytes of free blocks are kept.
+struct HostPool {
+    static constexpr size_t PIN_CAP = (size_t)8 << 30;
+    static constexpr size_t KEEP_CAP = (size_t)16 << 30;
+    struct Block {
+        void* p;
+        bool pinned;
+    };
+    std::mutex mu;
+    std::multimap<size_t, Block> free_blocks;  // capacity (bytes) -> block
+    size_t pinned_total = 0, free_total = 0;
+    // size classes: eight per power of two, at least 64 KiB
+    static size_t round_up(size_t b) {
+        size_t step = (size_t)64 << 10;
+        while (step * 16 <= b) step *= 2;
+        return (b + step - 1) / step * step;
+    }
+    // the smallest free block of at least `bytes`, else a new one
+    void* get(size_t bytes, size_t* cap, bool* pinned) {
+        const size_t want = round_up(bytes);
+        {
+            std::lock_guard<std::mutex> g(mu);
+            auto it = free_blocks.lower_bound(want);
+            if (it != free_blocks.end()) {
+                *cap = it->first;
+                *pinned = it->second.pinned;
+                void* p = it->second.p;
+                free_total -= it->first;
+                free_blocks.erase(it);
+                return p;
+            }
+        }
+        bool pin = false;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (pinned_total + want <= PIN_CAP) {
+                pinned_total += want;
+                pin = true;
+            }
+        }
+        void* p = nullptr;
+        if (pin && cudaMallocHost(&p, want) != cudaSuccess) {
+            cudaGetLastError();  // a failed pin is not an error of the call
+            p = nullptr;
+            std::lock_guard<std::mutex> g(mu);
+            pinned_total -= want;
+            pin = false;
+        }
+        if (!p) p = new unsigned char[want];
+        *cap = want;
+        *pinned = pin;
+        return p;
+    }
+    void put(void* p, size_t cap, bool pinned) {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (free_total + cap <= KEEP_CAP) {
+                free_blocks.emplace(cap, Block{p, pinned});
+                free_total += cap;
+                return;
+            }
+            if (pinned) pinned_total -= cap;
+        }
+        if (pinned) cudaFreeHost(p);
+        else delete[] static_cast<unsigned char*>(p);
+    }
+    ~HostPool() {
+        for (auto& kv : free_blocks) {
+            if (kv.second.pinned) cudaFreeHost(kv.second.p);
+            else delete[] static_cast<unsigned char*>(kv.second.p);
+        }
+    }
+};
+
 // Host array whose elements are left uninitialised on resize: a device copy
 // fills them at once, so zero-filling hundreds of MB first would be wasted.
 // A pinned array (page-locked, grown only) takes device copies at link speed
 // and keeps its pages from call to call; if pinning fails it falls back to
-// ordinary memory.
+// ordinary memory.  An array with a pool takes its block from the pool and
+// gives it back when released.
 template <class T>
 struct HostArr {
     T* p = nullptr;
     size_t n = 0, cap = 0;
     bool pinned = false, is_pinned = false;
+    HostPool* pool = nullptr;
     HostArr() = default;
     HostArr(const HostArr&) = delete;
     HostArr& operator=(const HostArr&) = delete;
@@ -91,12 +173,14 @@ struct HostArr {
         cap = o.cap;
         pinned = o.pinned;
         is_pinned = o.is_pinned;
+        pool = o.pool;
         o.p = nullptr;
         o.n = o.cap = 0;
     }
     void release() {
         if (p) {
-            if (is_pinned) cudaFreeHost(p);
+            if (pool) pool->put(p, cap * sizeof(T), is_pinned);
+            else if (is_pinned) cudaFreeHost(p);
             else delete[] p;
         }
         p = nullptr;
@@ -106,6 +190,15 @@ struct HostArr {
     void resize(size_t m) {
         if (m > cap) {
             release();
+            if (pool) {
+                size_t bytes = 0;
+                bool pin = false;
+                p = static_cast<T*>(pool->get(m * sizeof(T), &bytes, &pin));
+                is_pinned = pin;
+                cap = bytes / sizeof(T);
+                n = m;
+                return;
+            }
             void* q = nullptr;
             if (pinned && cudaMallocHost(&q, m * sizeof(T)) == cudaSuccess) {
                 p = static_cast<T*>(q);
@@ -129,6 +222,7 @@ struct HostResult {
     HostArr<uint32_t> counts;
     HostArr<uint64_t> hist;
     void set_pinned(bool on) { kmers.pinned = counts.pinned = hist.pinned = on; }
+    void set_pool(HostPool* p) { kmers.pool = counts.pool = hist.pool = p; }
 };
 
 struct ServeState;  // served form (hsk_serve.cu)
@@ -190,6 +284,7 @@ struct hsk_ctx {
     void* h_pin = nullptr;
     size_t h_pin_cap = 0;
 
+    HostPool result_pool;                // host blocks of batched and served results (outlives them)
     HostResult host_res;                 // result of the last hsk_count
     std::vector<HostResult> batch_res;   // results of the last hsk_count_batch
 

@@ -123,6 +123,7 @@ static void worker_main(hsk_ctx* parent, ServeState* S, int slot) {
         hsk_job job = T->job;
         lk.unlock();
         HostResult hr;
+        hr.set_pool(&parent->result_pool);
         int rc = hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo,
                                    job.hi, c->stream, c->in_reads, c->in_offsets, hr);
         std::string err = rc == HSK_OK ? std::string() : c->err_msg;
