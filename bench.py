@@ -300,6 +300,50 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
             "note": "latency = submit to completion; copies from pinned host memory inside every job"}
 
 
+def run_ablations(rs, local: int) -> dict:
+    """Diagnostics of the bucketing on the workload's reads (device-resident):
+    bucket balance (k-mers per bucket, from the S3 stage) at 256 and 4096
+    buckets, and a sweep of the minimizer length m with the whole count's
+    device time, the supermers formed and their mean k-mers."""
+    import torch
+    import paper_2407_07718_gb300 as hsk
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    d_reads = torch.from_numpy(rs.reads).to(dev)
+    d_offs = torch.from_numpy(rs.offsets.view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    balance, sweep = [], []
+    with hsk.Context(device=local) as ctx:
+        for B in (256, 4096):
+            bk = torch.zeros(B, dtype=torch.int64, device=dev)
+            br = torch.zeros(B + 1, dtype=torch.int64, device=dev)
+            _, nrec, _, _ = ctx.stage_supermers(d_reads, d_offs, rs.k, rs.m, B, bk, br, stream=stream)
+            torch.cuda.synchronize()
+            v = bk.cpu().numpy().astype(np.float64)
+            mean = v.mean()
+            balance.append({"n_buckets": B, "m": rs.m, "kmers_per_bucket_mean": mean,
+                            "max_over_mean": float(v.max() / mean), "min_over_mean": float(v.min() / mean),
+                            "cv": float(v.std() / mean), "n_supermers": int(nrec)})
+        for m in (11, 13, 15, 17, 19, 21):
+            if m > rs.k or m > 32:
+                continue
+            for _ in range(2):
+                r = ctx.count_device(d_reads, d_offs, rs.k, m, rs.lo, rs.hi, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                r = ctx.count_device(d_reads, d_offs, rs.k, m, rs.lo, rs.hi, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            sweep.append({"m": m, "ms_per_count": ms, "kmers_per_s": int(r.n_windows) / (ms / 1e3),
+                          "n_supermers": int(r.n_supermers),
+                          "kmers_per_supermer": int(r.n_windows) / max(1, int(r.n_supermers)),
+                          "n_distinct": int(r.n_distinct), "n_pairs": int(r.n_pairs)})
+    return {"bucket_balance": balance, "m_sweep": sweep}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -350,6 +394,8 @@ def main():
     ap.add_argument("--served-scale", type=float, default=1.0)
     ap.add_argument("--served-load", type=float, default=0.7)
     ap.add_argument("--served-budget", type=float, default=120e9)
+    ap.add_argument("--ablations", action="store_true",
+                    help="print one JSON line of bucketing diagnostics (bucket balance, m sweep) instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -359,6 +405,11 @@ def main():
     kw = 1 if rs.k <= 32 else 2
     config = {"workload": desc, "k": rs.k, "m": rs.m, "lo": rs.lo, "hi": rs.hi, "n_reads": rs.n_reads,
               "n_bases": rs.n_bases, "l2": "inputs larger than L2 (reads %.2f GB); no flush" % (rs.n_bases / 1e9)}
+
+    if args.ablations:
+        if rank == 0:
+            print(json.dumps({"ablations": run_ablations(rs, local), "config": config}))
+        return
 
     if args.impl == "reference":
         if rank != 0:
