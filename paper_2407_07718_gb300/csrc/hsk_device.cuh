@@ -109,13 +109,6 @@ __device__ __forceinline__ key128 canonical128(const key128& fwd, int k) {
     return key_lt(fwd, rc) ? fwd : rc;
 }
 
-// The n (1..64) mask bits starting at bit p of a most-significant-first mask.
-__device__ __forceinline__ u64 mask_bits(const u64* w, u64 p, int n) {
-    u64 i = p >> 6;
-    uint32_t off = (uint32_t)(p & 63);
-    u64 v = funnel64(w[i], w[i + 1], off);
-    return n >= 64 ? v : (v >> (64 - n));
-}
 
 // ---------------------------------------------------------------------------
 // device error flag and bounded waits
@@ -333,30 +326,6 @@ __device__ __forceinline__ key128 record_kmer128(const u64 (&W)[4], uint32_t j, 
     }
     return r;
 }
-
-// Key j of a tile of nr records staged in shared memory (s_rec, record_words
-// words each) whose k-mer counts have the exclusive prefix s_pre[0..nr]: the
-// key belongs to the last record r with s_pre[r] <= j.
-template <bool WIDE>
-__device__ __forceinline__ typename std::conditional<WIDE, key128, u64>::type
-tile_key(const u64* s_rec, const uint32_t* s_pre, uint32_t nr, uint32_t j, int k) {
-    constexpr int RW = WIDE ? 4 : 2;
-    uint32_t lo = 0, hi = nr;  // s_pre[lo] <= j < s_pre[hi]
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_pre[mid] <= j) lo = mid;
-        else hi = mid;
-    }
-    const uint32_t jj = j - s_pre[lo];
-    u64 W[4];
-    W[0] = s_rec[lo * RW];
-    W[1] = s_rec[lo * RW + 1];
-    W[2] = WIDE ? s_rec[lo * RW + 2] : 0ULL;
-    W[3] = WIDE ? s_rec[lo * RW + 3] : 0ULL;
-    if constexpr (WIDE) return canonical128(record_kmer128(W, jj, k), k);
-    else return canonical64(record_kmer64(W, jj, k), k);
-}
-
 
 // Calls f(j, key) for the canonical k-mers j = 0 .. n-1 of a supermer record
 // (record words W, bases packed from the most significant bit of W[0]): the
