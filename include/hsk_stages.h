@@ -127,6 +127,12 @@ uint64_t hsk_debug_last_overflow(hsk_ctx* ctx);
  * the context stays usable. */
 int hsk_debug_wait_timeout(hsk_ctx* ctx, uint32_t spin_limit);
 
+/* Self-check of the host block pool that holds the batched and served forms'
+ * results (size classes, best-fit reuse, the cap on kept blocks, arrays
+ * returning their blocks).  Host memory only: no device call is made.
+ * Returns 0, or the number of the first check that failed. */
+int hsk_debug_host_pool_check(void);
+
 /* Profiling hooks.  When enabled, each counting call on the context records
  * CUDA events on its own stream at the boundaries of its stages and adds the
  * device time between them to per-stage totals:

@@ -95,6 +95,7 @@ def load():
             "hsk_debug_allocated": ([P], u64),
             "hsk_debug_last_overflow": ([P], u64),
             "hsk_debug_wait_timeout": ([P, u32], C.c_int),
+            "hsk_debug_host_pool_check": ([], C.c_int),
             "hsk_profile_enable": ([P, i32], i32),
             "hsk_profile_read": ([P, C.POINTER(d), C.POINTER(u64), i32], i32),
             "hsk_launch_count": ([], u64),

@@ -1217,3 +1217,49 @@ extern "C" int hsk_debug_wait_timeout(hsk_ctx* c, uint32_t spin_limit) {
     CK(cudaStreamSynchronize(st));
     return rc;
 }
+
+// host block pool self-check (see hsk_stages.h); pinning is off (pin_cap = 0)
+// so that no device call is made
+extern "C" int hsk_debug_host_pool_check(void) {
+    HostPool pool;
+    pool.pin_cap = 0;
+    pool.keep_cap = (size_t)8 << 20;
+    // 1-3: size classes
+    if (HostPool::round_up(1) != ((size_t)64 << 10)) return 1;
+    if (HostPool::round_up((size_t)1 << 20) != ((size_t)1 << 20)) return 2;
+    const size_t b = ((size_t)3 << 20) + 1, r = HostPool::round_up(b);
+    if (r < b || (r - b) * 8 >= b) return 3;
+    // 4-6: a released block is reused by a request it fits, the smallest first
+    size_t c1 = 0, c4 = 0, c = 0;
+    bool pin = true;
+    void* p1 = pool.get((size_t)1 << 20, &c1, &pin);
+    if (!p1 || pin || c1 != ((size_t)1 << 20)) return 4;
+    void* p4 = pool.get((size_t)4 << 20, &c4, &pin);
+    pool.put(p1, c1, false);
+    pool.put(p4, c4, false);
+    void* q = pool.get((size_t)600 << 10, &c, &pin);
+    if (q != p1 || c != c1) return 5;
+    void* q2 = pool.get((size_t)2 << 20, &c, &pin);
+    if (q2 != p4 || c != c4) return 6;
+    // 7: past keep_cap a released block is freed, not kept
+    pool.put(q, c1, false);
+    pool.put(q2, c4, false);
+    size_t c16 = 0;
+    void* p16 = pool.get((size_t)16 << 20, &c16, &pin);
+    pool.put(p16, c16, false);
+    if (pool.free_total > pool.keep_cap || pool.free_total != c1 + c4) return 7;
+    // 8-10: arrays take blocks from the pool and give them back (moves included)
+    {
+        HostArr<uint64_t> a;
+        a.pool = &pool;
+        a.resize(100000);
+        if (!a.data() || a.size() != 100000 || a.cap < 100000) return 8;
+        uint64_t* d = a.data();
+        a.resize(50000);
+        if (a.data() != d) return 9;
+        HostArr<uint64_t> m(std::move(a));
+        if (m.data() != d || a.data() != nullptr || m.pool != &pool) return 10;
+    }
+    if (pool.free_total != c1 + c4) return 11;  // the array's block went back (it was one of the two)
+    return 0;
+}

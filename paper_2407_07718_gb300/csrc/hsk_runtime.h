@@ -68,11 +68,11 @@ struct DevResult {
 // ticket is released (or the next batch); freshly allocated pageable memory
 // would be faulted in page by page during that copy, and a new pinned block
 // costs a slow pinning call, so released blocks are kept and reused by later
-// jobs.  Blocks are pinned up to PIN_CAP bytes in total, pageable beyond;
-// at most KEEP_CAP bytes of free blocks are kept.
+// jobs.  Blocks are pinned up to pin_cap bytes in total, pageable beyond;
+// at most keep_cap bytes of free blocks are kept.
 struct HostPool {
-    static constexpr size_t PIN_CAP = (size_t)8 << 30;
-    static constexpr size_t KEEP_CAP = (size_t)16 << 30;
+    size_t pin_cap = (size_t)8 << 30;
+    size_t keep_cap = (size_t)16 << 30;
     struct Block {
         void* p;
         bool pinned;
@@ -80,7 +80,8 @@ struct HostPool {
     std::mutex mu;
     std::multimap<size_t, Block> free_blocks;  // capacity (bytes) -> block
     size_t pinned_total = 0, free_total = 0;
-    // size classes: eight per power of two, at least 64 KiB
+    // size classes: multiples of the smallest power of two (>= 64 KiB) above
+    // b / 16, so a block exceeds the request by less than b / 8
     static size_t round_up(size_t b) {
         size_t step = (size_t)64 << 10;
         while (step * 16 <= b) step *= 2;
@@ -104,7 +105,7 @@ struct HostPool {
         bool pin = false;
         {
             std::lock_guard<std::mutex> g(mu);
-            if (pinned_total + want <= PIN_CAP) {
+            if (pinned_total + want <= pin_cap) {
                 pinned_total += want;
                 pin = true;
             }
@@ -125,7 +126,7 @@ struct HostPool {
     void put(void* p, size_t cap, bool pinned) {
         {
             std::lock_guard<std::mutex> g(mu);
-            if (free_total + cap <= KEEP_CAP) {
+            if (free_total + cap <= keep_cap) {
                 free_blocks.emplace(cap, Block{p, pinned});
                 free_total += cap;
                 return;

@@ -54,6 +54,14 @@ def test_config_default_without_gpu(libpath):
     assert lib.hsk_count(None, None, None, 0, 31, 17, 2, 8, None) == hsk.HSK_EINVAL
 
 
+def test_host_pool_self_check(libpath):
+    """The host block pool behind the batched and served results (size
+    classes, best-fit reuse, the cap on kept blocks, arrays giving their
+    blocks back); host memory only, no device call."""
+    import paper_2407_07718_gb300 as hsk
+    assert hsk.load().hsk_debug_host_pool_check() == 0
+
+
 def test_oracle_and_library_share_no_code():
     """The oracle and the CUDA path include nothing from each other."""
     ora = open(os.path.join(ROOT, "oracle", "hsk_oracle.cpp")).read()
