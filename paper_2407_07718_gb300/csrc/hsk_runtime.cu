@@ -146,47 +146,49 @@ extern "C" int hsk_config_default(hsk_config* cfg) {
 }
 
 extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
-    if (!out) return HSK_EINVAL;
-    *out = nullptr;
-    hsk_config cfg;
-    if (cfg_in) cfg = *cfg_in;
-    else hsk_config_default(&cfg);
-    if (cfg.hist_len < 2 || (cfg.radix_bits != 0 && cfg.radix_bits != 8)) return HSK_EINVAL;
-    if (cfg.n_buckets && (cfg.n_buckets > HSK_MAX_BUCKETS || (cfg.n_buckets & (cfg.n_buckets - 1))))
-        return HSK_EINVAL;  // a power of two: the bucket is a mask of the hash
-    hsk_ctx* c = new hsk_ctx();
-    c->cfg = cfg;
-    cudaError_t e = cudaSetDevice(cfg.device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg.device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
-    for (int i = 0; i < HSK_MAX_PIPE && e == cudaSuccess; ++i)
-        e = cudaEventCreateWithFlags(&c->pipe_ev[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
-    size_t free_b = 0, total_b = 0;
-    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
-    if (e == cudaSuccess) e = cudaMalloc(&c->small, HSK_SMALL_BYTES);
-    if (e == cudaSuccess) e = cudaMemset(c->small, 0, HSK_SMALL_BYTES);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        return HSK_ECUDA;
-    }
-    c->budget = cfg.hbm_budget ? cfg.hbm_budget : (size_t)(free_b * 0.9);
-    c->host_res.set_pinned(true);  // hsk_count's results: reused from call to call
-    c->allocated = HSK_SMALL_BYTES;
-    char* s = (char*)c->small;
-    c->d_err = (int*)(s + 0);
-    c->d_max = (uint32_t*)(s + 8);
-    c->d_nheads = (uint64_t*)(s + 16);
-    c->d_nout = (uint64_t*)(s + 24);
-    c->d_ndesc = (uint64_t*)(s + 32);
-    c->d_nlocal = (uint64_t*)(s + 40);
-    c->d_ovstats = (uint64_t*)(s + 48);
-    c->counters = (uint32_t*)(s + 256);
-    *out = c;
-    return HSK_OK;
+    return hsk_guarded(nullptr, [&]() -> int {
+        if (!out) return HSK_EINVAL;
+        *out = nullptr;
+        hsk_config cfg;
+        if (cfg_in) cfg = *cfg_in;
+        else hsk_config_default(&cfg);
+        if (cfg.hist_len < 2 || (cfg.radix_bits != 0 && cfg.radix_bits != 8)) return HSK_EINVAL;
+        if (cfg.n_buckets && (cfg.n_buckets > HSK_MAX_BUCKETS || (cfg.n_buckets & (cfg.n_buckets - 1))))
+            return HSK_EINVAL;  // a power of two: the bucket is a mask of the hash
+        hsk_ctx* c = new hsk_ctx();
+        c->cfg = cfg;
+        cudaError_t e = cudaSetDevice(cfg.device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg.device);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
+        for (int i = 0; i < HSK_MAX_PIPE && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&c->pipe_ev[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+        size_t free_b = 0, total_b = 0;
+        if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+        if (e == cudaSuccess) e = cudaMalloc(&c->small, HSK_SMALL_BYTES);
+        if (e == cudaSuccess) e = cudaMemset(c->small, 0, HSK_SMALL_BYTES);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return HSK_ECUDA;
+        }
+        c->budget = cfg.hbm_budget ? cfg.hbm_budget : (size_t)(free_b * 0.9);
+        c->host_res.set_pinned(true);  // hsk_count's results: reused from call to call
+        c->allocated = HSK_SMALL_BYTES;
+        char* s = (char*)c->small;
+        c->d_err = (int*)(s + 0);
+        c->d_max = (uint32_t*)(s + 8);
+        c->d_nheads = (uint64_t*)(s + 16);
+        c->d_nout = (uint64_t*)(s + 24);
+        c->d_ndesc = (uint64_t*)(s + 32);
+        c->d_nlocal = (uint64_t*)(s + 40);
+        c->d_ovstats = (uint64_t*)(s + 48);
+        c->counters = (uint32_t*)(s + 256);
+        *out = c;
+        return HSK_OK;
+    });
 }
 
 extern "C" void hsk_destroy(hsk_ctx* c) {
@@ -954,19 +956,21 @@ static void to_public(const DevResult& R, hsk_result* out) {
 extern "C" int hsk_count_device(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets,
                                 uint64_t n_reads, uint64_t n_bases, int k, int m, uint32_t lo,
                                 uint32_t hi, void* stream, hsk_result* out) {
-    TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, lo, hi));
-    if (!out) return HSK_EINVAL;
-    if (n_bases > 0 && !d_reads) {
-        hsk_set_error(c, "NULL reads with n_bases > 0");
-        return HSK_EINVAL;
-    }
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    DevResult R;
-    int rc = hsk_run_count(c, d_reads, d_offsets, n_reads, n_bases, k, m, lo, hi, st, R);
-    if (rc != HSK_OK) return rc;
-    to_public(R, out);
-    return HSK_OK;
+    return hsk_guarded(c, [&]() -> int {
+        TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, lo, hi));
+        if (!out) return HSK_EINVAL;
+        if (n_bases > 0 && !d_reads) {
+            hsk_set_error(c, "NULL reads with n_bases > 0");
+            return HSK_EINVAL;
+        }
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        DevResult R;
+        int rc = hsk_run_count(c, d_reads, d_offsets, n_reads, n_bases, k, m, lo, hi, st, R);
+        if (rc != HSK_OK) return rc;
+        to_public(R, out);
+        return HSK_OK;
+    });
 }
 
 // Stage host buffers into context device memory, count, copy results back.
@@ -1040,13 +1044,15 @@ int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, ui
 
 extern "C" int hsk_count(hsk_ctx* c, const char* reads, const uint64_t* offsets, uint64_t n_reads,
                          int k, int m, uint32_t lo, uint32_t hi, hsk_result* out) {
-    TRY(check_args(c, reads, offsets, n_reads, k, m, lo, hi));
-    if (!out) return HSK_EINVAL;
-    CK(cudaSetDevice(c->cfg.device));
-    TRY(hsk_count_host_on(c, reads, offsets, n_reads, k, m, lo, hi, c->stream, c->in_reads,
-                          c->in_offsets, c->host_res));
-    to_public(c->host_res.R, out);
-    return HSK_OK;
+    return hsk_guarded(c, [&]() -> int {
+        TRY(check_args(c, reads, offsets, n_reads, k, m, lo, hi));
+        if (!out) return HSK_EINVAL;
+        CK(cudaSetDevice(c->cfg.device));
+        TRY(hsk_count_host_on(c, reads, offsets, n_reads, k, m, lo, hi, c->stream, c->in_reads,
+                              c->in_offsets, c->host_res));
+        to_public(c->host_res.R, out);
+        return HSK_OK;
+    });
 }
 
 extern "C" int hsk_result_copy(hsk_ctx* c, const hsk_result* r, uint64_t* kmers_dst,
@@ -1073,41 +1079,45 @@ extern "C" int hsk_result_copy(hsk_ctx* c, const hsk_result* r, uint64_t* kmers_
 extern "C" int hsk_stage_encode(hsk_ctx* c, const char* d_reads, uint64_t n_bases,
                                 const uint64_t* d_offsets, uint64_t n_reads, uint64_t* d_packed,
                                 uint64_t* d_invalid, uint64_t* d_start, void* stream) {
-    if (!c || !d_packed || !d_invalid || !d_start) return HSK_EINVAL;
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    c->zst = st;
-    uint64_t n_pw = (n_bases + 31) / 32, n_mw = (n_bases + 63) / 64;
-    CK(cudaMemsetAsync(c->small, 0, 64, st));
-    CK(cudaMemsetAsync(d_packed, 0, (n_pw + 4) * 8, st));
-    CK(cudaMemsetAsync(d_invalid, 0, (n_mw + 4) * 8, st));
-    CK(cudaMemsetAsync(d_start, 0, (n_mw + 4) * 8, st));
-    launch_mark_starts(d_offsets, n_reads, n_bases, d_start, c->d_err, st);
-    launch_encode(d_reads, n_bases, d_packed, d_invalid, n_pw, n_mw, st);
-    CK(cudaGetLastError());
-    return read_device_error(c, st);
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || !d_packed || !d_invalid || !d_start) return HSK_EINVAL;
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        c->zst = st;
+        uint64_t n_pw = (n_bases + 31) / 32, n_mw = (n_bases + 63) / 64;
+        CK(cudaMemsetAsync(c->small, 0, 64, st));
+        CK(cudaMemsetAsync(d_packed, 0, (n_pw + 4) * 8, st));
+        CK(cudaMemsetAsync(d_invalid, 0, (n_mw + 4) * 8, st));
+        CK(cudaMemsetAsync(d_start, 0, (n_mw + 4) * 8, st));
+        launch_mark_starts(d_offsets, n_reads, n_bases, d_start, c->d_err, st);
+        launch_encode(d_reads, n_bases, d_packed, d_invalid, n_pw, n_mw, st);
+        CK(cudaGetLastError());
+        return read_device_error(c, st);
+    });
 }
 
 extern "C" int hsk_stage_windows(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets,
                                  uint64_t n_reads, uint64_t n_bases, int k, int m, uint8_t* d_valid,
                                  uint64_t* d_key, uint64_t* d_minhash, void* stream) {
-    TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    c->zst = st;
-    CK(cudaMemsetAsync(c->small, 0, 64, st));
-    Encoded E;
-    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, false));
-    SmParams P;
-    fill_sm_params(c, E, k, m, 1, P);
-    uint64_t warp_tiles = (n_bases + 1023) / 1024;
-    P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->num_sms * 4, (warp_tiles + 7) / 8));
-    P.dump_valid = d_valid;
-    P.dump_key = d_key;
-    P.dump_minhash = d_minhash;
-    launch_supermer(SM_DUMP, P, st);
-    CK(cudaGetLastError());
-    return read_device_error(c, st);
+    return hsk_guarded(c, [&]() -> int {
+        TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        c->zst = st;
+        CK(cudaMemsetAsync(c->small, 0, 64, st));
+        Encoded E;
+        TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, false));
+        SmParams P;
+        fill_sm_params(c, E, k, m, 1, P);
+        uint64_t warp_tiles = (n_bases + 1023) / 1024;
+        P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->num_sms * 4, (warp_tiles + 7) / 8));
+        P.dump_valid = d_valid;
+        P.dump_key = d_key;
+        P.dump_minhash = d_minhash;
+        launch_supermer(SM_DUMP, P, st);
+        CK(cudaGetLastError());
+        return read_device_error(c, st);
+    });
 }
 
 extern "C" int hsk_stage_supermers(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets,
@@ -1116,90 +1126,98 @@ extern "C" int hsk_stage_supermers(hsk_ctx* c, const char* d_reads, const uint64
                                    uint64_t* d_bucket_rec, const uint64_t** d_records,
                                    uint64_t* n_records, int* record_words, int* max_kmers,
                                    void* stream) {
-    TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
-    if (n_buckets < 1 || n_buckets > HSK_MAX_BUCKETS || (n_buckets & (n_buckets - 1)) || !d_bucket_kmers || !d_bucket_rec || !d_records ||
-        !n_records || !record_words)
-        return HSK_EINVAL;
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    c->zst = st;
-    CK(cudaMemsetAsync(c->small, 0, 64, st));
-    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
-    c->ctr_used = 0;
-    Encoded E;
-    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, false));
-    Supermers S;
-    TRY(hsk_supermers(c, E, k, m, n_buckets, S, st, nullptr));
-    CK(cudaMemcpyAsync(d_bucket_kmers, c->bucket_kmers.p, (size_t)n_buckets * 8, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(d_bucket_rec, c->bucket_rec.p, ((size_t)n_buckets + 1) * 8, cudaMemcpyDeviceToDevice, st));
-    *d_records = S.records;
-    *n_records = S.n_records;
-    *record_words = S.rec_words;
-    if (max_kmers) *max_kmers = S.nmax;
-    return read_device_error(c, st);
+    return hsk_guarded(c, [&]() -> int {
+        TRY(check_args(c, d_reads, d_offsets, n_reads, k, m, 0, 0));
+        if (n_buckets < 1 || n_buckets > HSK_MAX_BUCKETS || (n_buckets & (n_buckets - 1)) || !d_bucket_kmers || !d_bucket_rec || !d_records ||
+            !n_records || !record_words)
+            return HSK_EINVAL;
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        c->zst = st;
+        CK(cudaMemsetAsync(c->small, 0, 64, st));
+        CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+        c->ctr_used = 0;
+        Encoded E;
+        TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, false));
+        Supermers S;
+        TRY(hsk_supermers(c, E, k, m, n_buckets, S, st, nullptr));
+        CK(cudaMemcpyAsync(d_bucket_kmers, c->bucket_kmers.p, (size_t)n_buckets * 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(d_bucket_rec, c->bucket_rec.p, ((size_t)n_buckets + 1) * 8, cudaMemcpyDeviceToDevice, st));
+        *d_records = S.records;
+        *n_records = S.n_records;
+        *record_words = S.rec_words;
+        if (max_kmers) *max_kmers = S.nmax;
+        return read_device_error(c, st);
+    });
 }
 
 extern "C" int hsk_stage_sort(hsk_ctx* c, uint64_t* d_keys, uint64_t n, int key_words, int key_bits,
                               void* stream) {
-    if (!c || (n && !d_keys) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
-        key_bits > 64 * key_words)
-        return HSK_EINVAL;
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    c->zst = st;
-    CK(cudaMemsetAsync(c->small, 0, 64, st));
-    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
-    c->ctr_used = 0;
-    if (n <= 1) return HSK_OK;
-    TRY(plain_sort(c, d_keys, nullptr, n, key_words, key_bits, c->alt, nullptr, st));
-    return read_device_error(c, st);
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || (n && !d_keys) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
+            key_bits > 64 * key_words)
+            return HSK_EINVAL;
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        c->zst = st;
+        CK(cudaMemsetAsync(c->small, 0, 64, st));
+        CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+        c->ctr_used = 0;
+        if (n <= 1) return HSK_OK;
+        TRY(plain_sort(c, d_keys, nullptr, n, key_words, key_bits, c->alt, nullptr, st));
+        return read_device_error(c, st);
+    });
 }
 
 extern "C" int hsk_stage_rle(hsk_ctx* c, const uint64_t* d_sorted, uint64_t n, int key_words,
                              uint32_t lo, uint32_t hi, void* stream, hsk_result* out) {
-    if (!c || !out || (n && !d_sorted) || (key_words != 1 && key_words != 2) || lo > hi) return HSK_EINVAL;
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    c->zst = st;
-    const uint32_t H = c->cfg.hist_len;
-    TRY(hsk_ensure(c, c->hist, (size_t)H * 8, false));
-    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)H * 8, st));
-    CK(cudaMemsetAsync(c->small, 0, 64, st));
-    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
-    c->ctr_used = 0;
-    Output O;
-    TRY(hsk_rle_chunk(c, d_sorted, n, key_words, lo, hi, H, (uint64_t*)c->hist.p, O, st));
-    uint32_t mx = 0;
-    TRY(read_device_error(c, st, &mx));
-    DevResult R;
-    memset(&R, 0, sizeof R);
-    R.n_pairs = O.n_pairs;
-    R.n_distinct = O.n_distinct;
-    R.n_windows = n;
-    R.max_count = mx;
-    R.key_words = key_words;
-    R.kmers = (const uint64_t*)c->out_keys.p;
-    R.counts = (const uint32_t*)c->out_counts.p;
-    R.hist = (const uint64_t*)c->hist.p;
-    R.hist_len = H;
-    R.n_chunks = 1;
-    to_public(R, out);
-    return HSK_OK;
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || !out || (n && !d_sorted) || (key_words != 1 && key_words != 2) || lo > hi) return HSK_EINVAL;
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        c->zst = st;
+        const uint32_t H = c->cfg.hist_len;
+        TRY(hsk_ensure(c, c->hist, (size_t)H * 8, false));
+        CK(cudaMemsetAsync(c->hist.p, 0, (size_t)H * 8, st));
+        CK(cudaMemsetAsync(c->small, 0, 64, st));
+        CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+        c->ctr_used = 0;
+        Output O;
+        TRY(hsk_rle_chunk(c, d_sorted, n, key_words, lo, hi, H, (uint64_t*)c->hist.p, O, st));
+        uint32_t mx = 0;
+        TRY(read_device_error(c, st, &mx));
+        DevResult R;
+        memset(&R, 0, sizeof R);
+        R.n_pairs = O.n_pairs;
+        R.n_distinct = O.n_distinct;
+        R.n_windows = n;
+        R.max_count = mx;
+        R.key_words = key_words;
+        R.kmers = (const uint64_t*)c->out_keys.p;
+        R.counts = (const uint32_t*)c->out_counts.p;
+        R.hist = (const uint64_t*)c->hist.p;
+        R.hist_len = H;
+        R.n_chunks = 1;
+        to_public(R, out);
+        return HSK_OK;
+    });
 }
 
 extern "C" int hsk_stage_order(hsk_ctx* c, uint64_t* d_keys, uint32_t* d_counts, uint64_t n,
                                int key_words, int key_bits, void* stream) {
-    if (!c || (n && (!d_keys || !d_counts)) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
-        key_bits > 64 * key_words)
-        return HSK_EINVAL;
-    CK(cudaSetDevice(c->cfg.device));
-    cudaStream_t st = (cudaStream_t)stream;
-    c->zst = st;
-    CK(cudaMemsetAsync(c->small, 0, 64, st));
-    CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
-    c->ctr_used = 0;
-    TRY(hsk_order_pairs(c, d_keys, d_counts, n, key_words, key_bits, st, 0));
-    return read_device_error(c, st);
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || (n && (!d_keys || !d_counts)) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
+            key_bits > 64 * key_words)
+            return HSK_EINVAL;
+        CK(cudaSetDevice(c->cfg.device));
+        cudaStream_t st = (cudaStream_t)stream;
+        c->zst = st;
+        CK(cudaMemsetAsync(c->small, 0, 64, st));
+        CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
+        c->ctr_used = 0;
+        TRY(hsk_order_pairs(c, d_keys, d_counts, n, key_words, key_bits, st, 0));
+        return read_device_error(c, st);
+    });
 }
 
 extern "C" int hsk_debug_wait_timeout(hsk_ctx* c, uint32_t spin_limit) {

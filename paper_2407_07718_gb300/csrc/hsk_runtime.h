@@ -8,6 +8,8 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -325,6 +327,25 @@ void hsk_set_error(hsk_ctx* c, const char* fmt, ...);
         int rc_ = (x);              \
         if (rc_ != HSK_OK) return rc_; \
     } while (0)
+
+// Runs the body of a C entry point so that no C++ exception crosses the C
+// boundary: a failed host allocation returns HSK_ENOMEM, anything else
+// HSK_ECUDA, with the reason in the context's error text (when there is one).
+template <class F>
+int hsk_guarded(hsk_ctx* c, F&& body) {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        if (c) hsk_set_error(c, "host memory allocation failed");
+        return HSK_ENOMEM;
+    } catch (const std::exception& e) {
+        if (c) hsk_set_error(c, "host exception: %s", e.what());
+        return HSK_ECUDA;
+    } catch (...) {
+        if (c) hsk_set_error(c, "unknown host exception");
+        return HSK_ECUDA;
+    }
+}
 int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new);
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,

@@ -124,8 +124,10 @@ static void worker_main(hsk_ctx* parent, ServeState* S, int slot) {
         lk.unlock();
         HostResult hr;
         hr.set_pool(&parent->result_pool);
-        int rc = hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo,
-                                   job.hi, c->stream, c->in_reads, c->in_offsets, hr);
+        int rc = hsk_guarded(c, [&]() -> int {
+            return hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo, job.hi,
+                                     c->stream, c->in_reads, c->in_offsets, hr);
+        });
         std::string err = rc == HSK_OK ? std::string() : c->err_msg;
         lk.lock();
         T->rc = rc;
@@ -205,23 +207,25 @@ static int validate_job(hsk_ctx* c, const hsk_job* j) {
 }
 
 extern "C" int hsk_submit(hsk_ctx* c, const hsk_job* job, uint64_t* ticket) {
-    if (!c || !ticket) return HSK_EINVAL;
-    int rc = validate_job(c, job);
-    if (rc != HSK_OK) return rc;
-    rc = serve_start(c);
-    if (rc != HSK_OK) return rc;
-    ServeState* S = c->serve;
-    auto T = std::make_unique<Ticket>();
-    T->job = *job;
-    T->est = job_estimate(*job);
-    T->t_submit = now_s();
-    std::lock_guard<std::mutex> g(S->mu);
-    uint64_t id = S->next_ticket++;
-    S->tickets[id] = std::move(T);
-    S->queue.push_back(id);
-    *ticket = id;
-    S->cv_work.notify_all();
-    return HSK_OK;
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || !ticket) return HSK_EINVAL;
+        int rc = validate_job(c, job);
+        if (rc != HSK_OK) return rc;
+        rc = serve_start(c);
+        if (rc != HSK_OK) return rc;
+        ServeState* S = c->serve;
+        auto T = std::make_unique<Ticket>();
+        T->job = *job;
+        T->est = job_estimate(*job);
+        T->t_submit = now_s();
+        std::lock_guard<std::mutex> g(S->mu);
+        uint64_t id = S->next_ticket++;
+        S->tickets[id] = std::move(T);
+        S->queue.push_back(id);
+        *ticket = id;
+        S->cv_work.notify_all();
+        return HSK_OK;
+    });
 }
 
 extern "C" int hsk_poll(hsk_ctx* c, uint64_t ticket, int* done) {
@@ -253,21 +257,23 @@ static void fill_out(const HostResult& hr, hsk_result* out) {
 }
 
 extern "C" int hsk_wait(hsk_ctx* c, uint64_t ticket, hsk_result* out) {
-    if (!c || !out) return HSK_EINVAL;
-    if (!c->serve) return HSK_ENOTFOUND;
-    ServeState* S = c->serve;
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->tickets.find(ticket);
-    if (it == S->tickets.end()) return HSK_ENOTFOUND;
-    Ticket* T = it->second.get();
-    S->cv_done.wait(lk, [&] { return T->state == T_DONE || T->state == T_CANCELED; });
-    if (T->state == T_CANCELED) return HSK_ECANCELED;
-    if (T->rc != HSK_OK) {
-        c->err_msg = T->err;
-        return T->rc;
-    }
-    fill_out(T->res, out);
-    return HSK_OK;
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || !out) return HSK_EINVAL;
+        if (!c->serve) return HSK_ENOTFOUND;
+        ServeState* S = c->serve;
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->tickets.find(ticket);
+        if (it == S->tickets.end()) return HSK_ENOTFOUND;
+        Ticket* T = it->second.get();
+        S->cv_done.wait(lk, [&] { return T->state == T_DONE || T->state == T_CANCELED; });
+        if (T->state == T_CANCELED) return HSK_ECANCELED;
+        if (T->rc != HSK_OK) {
+            c->err_msg = T->err;
+            return T->rc;
+        }
+        fill_out(T->res, out);
+        return HSK_OK;
+    });
 }
 
 extern "C" int hsk_cancel(hsk_ctx* c, uint64_t ticket) {
@@ -313,58 +319,60 @@ extern "C" int hsk_ticket_times(hsk_ctx* c, uint64_t ticket, double* queued_s, d
 // batched form: the jobs go through the serving slots, largest first
 // ---------------------------------------------------------------------------
 extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs, hsk_result* outs) {
-    if (!c || (n_jobs && (!jobs || !outs))) return HSK_EINVAL;
-    for (uint32_t i = 0; i < n_jobs; ++i) {
-        int rc = validate_job(c, jobs + i);
-        if (rc != HSK_OK) return rc;
-    }
-    CK(cudaSetDevice(c->cfg.device));
-    c->batch_res.clear();
-    c->batch_res.resize(n_jobs);
-    if (n_jobs == 0) return HSK_OK;
-    TRY(serve_start(c));
-    ServeState* S = c->serve;
-    // Largest job first (longest-processing-time order): with the slots
-    // running side by side, the big jobs start early and the small ones fill
-    // the gaps, which shortens the makespan.
-    std::vector<uint32_t> order(n_jobs);
-    for (uint32_t i = 0; i < n_jobs; ++i) order[i] = i;
-    auto bases = [&](uint32_t i) { return jobs[i].n_reads ? jobs[i].offsets[jobs[i].n_reads] : 0; };
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return bases(a) > bases(b); });
-    std::vector<uint64_t> ids(n_jobs);
-    {
-        std::lock_guard<std::mutex> g(S->mu);
-        for (uint32_t i : order) {
-            auto T = std::make_unique<Ticket>();
-            T->job = jobs[i];
-            T->est = job_estimate(jobs[i]);
-            T->t_submit = now_s();
-            uint64_t id = S->next_ticket++;
-            S->tickets[id] = std::move(T);
-            S->queue.push_back(id);
-            ids[i] = id;
-        }
-    }
-    S->cv_work.notify_all();
-    int first_rc = HSK_OK;
-    std::string first_err;
-    {
-        std::unique_lock<std::mutex> lk(S->mu);
+    return hsk_guarded(c, [&]() -> int {
+        if (!c || (n_jobs && (!jobs || !outs))) return HSK_EINVAL;
         for (uint32_t i = 0; i < n_jobs; ++i) {
-            Ticket* T = S->tickets[ids[i]].get();
-            S->cv_done.wait(lk, [&] { return T->state == T_DONE; });
-            if (T->rc != HSK_OK && first_rc == HSK_OK) {
-                first_rc = T->rc;
-                first_err = "job " + std::to_string(i) + ": " + T->err;
-            }
-            c->batch_res[i] = std::move(T->res);
-            S->tickets.erase(ids[i]);
+            int rc = validate_job(c, jobs + i);
+            if (rc != HSK_OK) return rc;
         }
-    }
-    if (first_rc != HSK_OK) {
-        c->err_msg = first_err;
-        return first_rc;
-    }
-    for (uint32_t i = 0; i < n_jobs; ++i) fill_out(c->batch_res[i], outs + i);
-    return HSK_OK;
+        CK(cudaSetDevice(c->cfg.device));
+        c->batch_res.clear();
+        c->batch_res.resize(n_jobs);
+        if (n_jobs == 0) return HSK_OK;
+        TRY(serve_start(c));
+        ServeState* S = c->serve;
+        // Largest job first (longest-processing-time order): with the slots
+        // running side by side, the big jobs start early and the small ones fill
+        // the gaps, which shortens the makespan.
+        std::vector<uint32_t> order(n_jobs);
+        for (uint32_t i = 0; i < n_jobs; ++i) order[i] = i;
+        auto bases = [&](uint32_t i) { return jobs[i].n_reads ? jobs[i].offsets[jobs[i].n_reads] : 0; };
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return bases(a) > bases(b); });
+        std::vector<uint64_t> ids(n_jobs);
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            for (uint32_t i : order) {
+                auto T = std::make_unique<Ticket>();
+                T->job = jobs[i];
+                T->est = job_estimate(jobs[i]);
+                T->t_submit = now_s();
+                uint64_t id = S->next_ticket++;
+                S->tickets[id] = std::move(T);
+                S->queue.push_back(id);
+                ids[i] = id;
+            }
+        }
+        S->cv_work.notify_all();
+        int first_rc = HSK_OK;
+        std::string first_err;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (uint32_t i = 0; i < n_jobs; ++i) {
+                Ticket* T = S->tickets[ids[i]].get();
+                S->cv_done.wait(lk, [&] { return T->state == T_DONE; });
+                if (T->rc != HSK_OK && first_rc == HSK_OK) {
+                    first_rc = T->rc;
+                    first_err = "job " + std::to_string(i) + ": " + T->err;
+                }
+                c->batch_res[i] = std::move(T->res);
+                S->tickets.erase(ids[i]);
+            }
+        }
+        if (first_rc != HSK_OK) {
+            c->err_msg = first_err;
+            return first_rc;
+        }
+        for (uint32_t i = 0; i < n_jobs; ++i) fill_out(c->batch_res[i], outs + i);
+        return HSK_OK;
+    });
 }
