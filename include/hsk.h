@@ -41,7 +41,7 @@ extern "C" {
 
 #define HSK_OK 0
 #define HSK_EINVAL (-1)     /* bad argument: k, m, lo/hi, pointers, offsets */
-#define HSK_ENOMEM (-2)     /* the job does not fit the context's HBM budget */
+#define HSK_ENOMEM (-2)     /* the job does not fit the context's HBM budget, or host memory ran out */
 #define HSK_ECUDA (-3)      /* a CUDA runtime call failed; see hsk_last_error */
 #define HSK_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
 #define HSK_ECANCELED (-5)  /* the job was cancelled before it ran */
