@@ -839,11 +839,17 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     prof_mark(c, st, -1);
     Output O;
     Encoded E;
-    TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, pipe != nullptr));
+    {
+        NvtxRange r("S1 encode");
+        TRY(hsk_encode_into(c, d_reads, n_bases, d_offsets, n_reads, c->pk, c->iv, c->rs, E, st, pipe != nullptr));
+    }
     prof_mark(c, st, 0);
     Supermers S;
     uint32_t B = hsk_pick_buckets(c, n_bases, k);
-    TRY(hsk_supermers(c, E, k, m, B, S, st, pipe));
+    {
+        NvtxRange r("S2-S3 supermers");
+        TRY(hsk_supermers(c, E, k, m, B, S, st, pipe));
+    }
     prof_mark(c, st, 2);
     R.n_windows = S.n_kmers;
     R.n_supermers = S.n_records;
@@ -862,11 +868,13 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
             const uint64_t per_group = 256ull * local_cap(kw) / 3;
             const uint32_t C_want = (uint32_t)std::min<uint64_t>(ch.second - ch.first,
                                                                  std::max<uint64_t>(1, nk / per_group));
+            NvtxRange r("S4-S5 on-chip sort and count");
             TRY(local_chunk(c, S, group_buckets(S, ch.first, ch.second, C_want), nk, k, lo, hi, H, O, st));
             unordered = true;
             continue;
         }
         // segments: groups of buckets sorted independently, tiles interleaved
+        NvtxRange r("S4-S5 global radix sort and count");
         uint32_t C_want = (uint32_t)std::min<uint64_t>({(uint64_t)HSK_SEGMENTS, ch.second - ch.first,
                                                         std::max<uint64_t>(1, nk / HSK_MIN_SEGMENT_KMERS)});
         std::vector<uint32_t> cut = group_buckets(S, ch.first, ch.second, C_want);
@@ -912,8 +920,10 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
         TRY(hsk_rle_chunk(c, sorted, nk, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
         prof_mark(c, st, 5);
     }
-    if (total_segments > 1 || unordered)
+    if (total_segments > 1 || unordered) {
+        NvtxRange r("S6 order");
         TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st, hi));
+    }
     prof_mark(c, st, 6);
     CK(cudaEventRecord(c->ev1, st));
     uint32_t mx = 0;

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/hsk.h"
 
@@ -327,6 +328,15 @@ void hsk_set_error(hsk_ctx* c, const char* fmt, ...);
         int rc_ = (x);              \
         if (rc_ != HSK_OK) return rc_; \
     } while (0)
+
+// A named NVTX range over a scope (a profiler groups the scope's launches
+// under the name; without a profiler attached the calls do nothing).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Runs the body of a C entry point so that no C++ exception crosses the C
 // boundary: a failed host allocation returns HSK_ENOMEM, anything else
