@@ -307,3 +307,54 @@ def test_supermers_against_brute_force_runs(n_buckets):
         per[b] += 1
     assert bk.tolist() == [per[b] for b in range(n_buckets)]
     assert int(sn.sum()) == len(pos)
+
+
+# --- encoding stage (Sec. 2.2) and the window count ----------------------------
+
+def test_encode_matches_the_byte_table():
+    """Every one of the 256 byte values against the hand-written table in
+    tests/golden/encode_table.json: a swapped code or a wrong invalid flag on
+    any byte (lower case, N, IUPAC, high bytes) fails here."""
+    rows = json.load(open(os.path.join(GOLDEN, "encode_table.json")))["rows"]
+    assert [r[0] for r in rows] == list(range(256))
+    all_bytes = np.arange(256, dtype=np.uint8)
+    code, inv = oracle.encode(all_bytes)
+    assert code.tolist() == [r[1] for r in rows]
+    assert inv.tolist() == [r[2] for r in rows]
+    # the same bytes in another order and repeated: the code is per byte, position-free
+    perm = np.random.default_rng(4).permutation(np.tile(all_bytes, 3))
+    code2, inv2 = oracle.encode(perm)
+    assert code2.tolist() == [rows[b][1] for b in perm.tolist()]
+    assert inv2.tolist() == [rows[b][2] for b in perm.tolist()]
+    # exactly four valid bytes, with four distinct codes
+    assert sorted(r[1] for r in rows if r[2] == 0) == [0, 1, 2, 3]
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 31, 32, 33, 55, 64])
+def test_n_windows_matches_closed_form(k):
+    """oracle.n_windows (the full-size window-count checker) against the closed
+    form: the sum over maximal stretches of upper-case ACGT bytes, within each
+    read, of max(0, L - k + 1)."""
+    reads, offs = datagen.random_reads(31 + k, 400, 0, 300, p_invalid=0.01, invalid=b"NnRx\x00\xff")
+    extra = [b"", b"A" * (k - 1), b"A" * k, b"C" * (k + 5) + b"N" + b"G" * k]
+    blobs = [reads[int(offs[i]):int(offs[i + 1])].tobytes() for i in range(offs.size - 1)] + extra
+
+    def closed_form(bs):
+        total = 0
+        for b in bs:
+            run = 0
+            for ch in b + b"$":
+                if ch in b"ACGT":
+                    run += 1
+                else:
+                    total += max(0, run - k + 1)
+                    run = 0
+        return total
+
+    r = np.frombuffer(b"".join(blobs), np.uint8).copy()
+    o = np.zeros(len(blobs) + 1, np.uint64)
+    o[1:] = np.cumsum([len(b) for b in blobs])
+    assert oracle.n_windows(r, o, k) == closed_form(blobs)
+    # windows never cross a read boundary: one read holding all bytes has more
+    one = np.array([0, r.size], np.uint64)
+    assert oracle.n_windows(r, one, k) == closed_form([b"".join(blobs)])
