@@ -50,17 +50,40 @@ UNIT = "k-mers/s"
 #   dram  : DRAM bytes read + written per key (both passes)
 # The commands that produced them are in profiles/.
 NCU_PER_KEY = {
-    # long-read workload, k=31: k_local_sort passes 0 + 1, smsp__inst_executed.sum at full
-    # size (1.4955 G keys); DRAM bytes from the 0.1-scale case (149.6 M keys), per key
-    ("long_read", "28196a6506179be2"): {"inst": 11.5679, "dram": 8.3418},
+    # long-read workload, k=31: k_local_sort passes 0 + 1, smsp__inst_executed.sum and DRAM
+    # bytes from the 0.1-scale case (149.6 M keys), per key
+    ("long_read", "28196a6506179be2"): {"inst": 11.384, "dram": 8.3418},
 }
-# Issue slots of one GB300: 152 SMs x 4 warp schedulers x 1 warp instruction
-# per cycle (times the SM clock sampled during the run).
-ISSUE_SLOTS_PER_CYCLE = 152 * 4
+# Warp schedulers per SM (Blackwell): each issues at most one warp instruction
+# per cycle; the issue peak is SMs (queried from the device) x this x the SM
+# clock sampled during the run.
+SCHEDULERS_PER_SM = 4
 
 
 def source_sha(path: str) -> str:
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def host_cpu() -> dict:
+    """Core count (nproc) and CPU model of the host running the oracle."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model or "unknown"}
 
 
 def measured_peaks() -> dict:
@@ -300,6 +323,39 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
             "note": "latency = submit to completion; copies from pinned host memory inside every job"}
 
 
+def bench_second_workload(hsk, local: int, name: str, steps: int, warmup: int) -> dict:
+    """Device-resident steps of a second plain workload (default: the
+    short-read set at k=55 with 128-bit keys), timed like the main line."""
+    import torch
+    rs, desc = make_workload(name, 1.0)
+    dev = torch.device("cuda", local)
+    d_reads = torch.from_numpy(rs.reads).to(dev)
+    d_offs = torch.from_numpy(rs.offsets.view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    with hsk.Context(device=local) as ctx:
+        for _ in range(max(3, warmup)):
+            r = ctx.count_device(d_reads, d_offs, rs.k, rs.m, rs.lo, rs.hi, stream=stream)
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            r = ctx.count_device(d_reads, d_offs, rs.k, rs.m, rs.lo, rs.hi, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        stage_ms, _ = ctx.profile_read(reset=True)
+        out = {"workload": desc, "k": rs.k, "m": rs.m, "lo": rs.lo, "hi": rs.hi, "n_bases": rs.n_bases,
+               "n_windows": int(r.n_windows), "n_pairs": int(r.n_pairs), "n_distinct": int(r.n_distinct),
+               "steps": steps, "ms_per_step": ms, "value": int(r.n_windows) / (ms / 1e3), "unit": UNIT,
+               "dtype": "u64" if rs.k <= 32 else "u128",
+               "stages_ms_per_step": {n: v / steps for n, v in zip(hsk.Context.STAGES, stage_ms)}}
+    del d_reads, d_offs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ablations(rs, local: int) -> dict:
     """Diagnostics of the bucketing on the workload's reads (device-resident):
     bucket balance (k-mers per bucket, from the S3 stage) at 256 and 4096
@@ -388,6 +444,9 @@ def main():
                     help="windows in the oracle's bounded sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--second-workload", default="short_read", choices=["short_read", "long_read", "none"],
+                    help="a second plain workload reported under its own key (default: short-read, k=55)")
+    ap.add_argument("--second-steps", type=int, default=5)
     ap.add_argument("--batched-sets", type=int, default=256)
     ap.add_argument("--batched-scale", type=float, default=1.0)
     ap.add_argument("--served-requests", type=int, default=200)
@@ -425,8 +484,9 @@ def main():
                 "steps": steps, "warmup": args.warmup, "ms_per_step": tot / steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64" if kw == 1 else "u128",
                 "data": "synthetic", "config": config,
-                "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
-                                 "sample": f"first {nreads} reads of the workload ({nw} windows), single-thread C++ std::sort oracle"},
+                "cpu_baseline": dict({"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                                      "sample": f"first {nreads} reads of the workload ({nw} windows), single-thread C++ std::sort oracle"},
+                                     **host_cpu()),
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -494,7 +554,8 @@ def main():
         launch_ms = stage_ms[4] / args.steps
         sha = source_sha(os.path.join(ROOT, "paper_2407_07718_gb300", "csrc", "k_local.cu"))
         cnt = NCU_PER_KEY.get((args.workload, sha))
-        peak_issue = ISSUE_SLOTS_PER_CYCLE * clk_mhz / 1e3  # G warp-instructions / s
+        n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_issue = n_sms * SCHEDULERS_PER_SM * clk_mhz / 1e3  # G warp-instructions / s
         inst = cnt["inst"] * n_windows if cnt else None
         achieved = inst / (launch_ms / 1e3) / 1e9 if inst and launch_ms > 0 else None
         hbm_bytes = n_windows * kb + int(res.n_pairs) * (kb + 4)
@@ -503,7 +564,7 @@ def main():
                     "achieved": achieved, "peak": peak_issue, "unit": "G warp-instructions/s",
                     "frac": achieved / peak_issue if achieved else None,
                     "traffic": cnt["dram"] * n_windows if cnt else None,
-                    "peak_source": f"issue slots: 152 SMs x 4 schedulers x {clk_mhz:.0f} MHz (sampled)",
+                    "peak_source": f"issue slots: {n_sms} SMs x {SCHEDULERS_PER_SM} schedulers x {clk_mhz:.0f} MHz (sampled)",
                     "inst_per_launch": inst, "launch_ms": launch_ms,
                     "hbm_view": {"bytes_per_launch": hbm_bytes, "achieved": hbm_achieved, "unit": "GB/s",
                                  "frac": hbm_achieved / peaks["hbm_gbs"],
@@ -551,12 +612,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         nw, times, nreads = run_cpu_oracle(rs, args.cpu_windows)
-        cpu = {"value": nw / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {nreads} reads of the workload ({nw} windows), single-thread C++ std::sort oracle, {times[0]:.1f} s"}
+        cpu = dict({"value": nw / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"first {nreads} reads of the workload ({nw} windows), single-thread C++ std::sort oracle, {times[0]:.1f} s"},
+                   **host_cpu())
 
     ctx.close()
     del d_reads, d_offs
     forms = {}
+    if rank == 0 and world == 1 and args.second_workload not in ("none", args.workload):
+        torch.cuda.empty_cache()
+        forms[args.second_workload] = bench_second_workload(hsk, local, args.second_workload, args.second_steps,
+                                                            args.warmup)
     if rank == 0 and world == 1 and not args.no_forms:
         torch.cuda.empty_cache()
         forms["batched"] = bench_batched(hsk, local, args.batched_sets, args.batched_scale)

@@ -72,7 +72,8 @@ int hsk_stage_supermers(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_off
 /* Stage S4, LSD radix sort of packed keys (Sec. 3.1: equal k-mers become
  * adjacent).  Sorts n keys of key_words uint64 words (1, or 2 as {lo, hi})
  * in place, ascending, looking only at the low key_bits bits (1..128); the
- * other bits must be zero.  Scratch is context-owned. */
+ * other bits must be zero.  d_keys is 8-byte aligned (16-byte aligned for
+ * key_words = 2), else HSK_EINVAL.  Scratch is context-owned. */
 int hsk_stage_sort(hsk_ctx* ctx, uint64_t* d_keys, uint64_t n, int key_words, int key_bits,
                    void* stream);
 
@@ -85,7 +86,9 @@ int hsk_stage_rle(hsk_ctx* ctx, const uint64_t* d_sorted, uint64_t n, int key_wo
 
 /* Stage S6, output order: sort n (key, count) pairs by key, ascending, in
  * place (keys of key_words words with key_bits significant bits; counts move
- * with their keys).  Keys must be distinct for the order to be unique. */
+ * with their keys).  Keys must be distinct for the order to be unique.
+ * d_keys is 8-byte aligned (16-byte aligned for key_words = 2) and d_counts
+ * 4-byte aligned, else HSK_EINVAL. */
 int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t n,
                     int key_words, int key_bits, void* stream);
 
@@ -102,11 +105,19 @@ int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t
  * HSK_NOALLOC_MAX_KEYS_U64 (key_words = 1) or HSK_NOALLOC_MAX_KEYS_U128
  * (key_words = 2), larger n returns HSK_EOVERFLOW and does nothing.  The
  * first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  All calls
- * share the array, so calls that overlap on the GPU (other streams, other host
- * threads) race.  No context is needed; the work is ordered on `stream` and
- * complete on return.  HSK_EINVAL for bad arguments, HSK_ECUDA / HSK_ETIMEOUT
- * as elsewhere. */
+ * device address and keeps it for the life of the process; after a
+ * cudaDeviceReset that address is stale, so the entry point must not be
+ * called again.  All calls share the array, so calls that overlap on the GPU
+ * (other streams, other host threads) race.  No context is needed.  The call
+ * is synchronous: the work is ordered on `stream` and the call reads the
+ * result status back and synchronizes `stream` before it returns, so it
+ * cannot be called while `stream` is being captured into a CUDA graph.
+ * d_keys must be 8-byte aligned for key_words = 1 (it need not be 16-byte
+ * aligned) and 16-byte aligned for key_words = 2.  Returns HSK_EINVAL for bad
+ * arguments (a misaligned d_keys included), HSK_ETIMEOUT as elsewhere, and HSK_ECUDA when a CUDA call or
+ * launch of this call fails -- or, without doing anything, when a launch
+ * error from the caller's earlier work is still pending (it is not
+ * cleared). */
 #define HSK_NOALLOC_MAX_KEYS_U64 (1u << 20)
 #define HSK_NOALLOC_MAX_KEYS_U128 (1u << 19)
 int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words, int key_bits, void* stream);

@@ -124,6 +124,8 @@ static uint32_t bucket_of(uint64_t minhash, uint32_t n_buckets) {
 
 extern "C" {
 
+uint64_t oracle_n_windows(const char* reads, const uint64_t* offsets, uint64_t n_reads, int k);
+
 // Result of oracle_count.  Arrays are malloc'ed here; release with oracle_free.
 typedef struct {
     uint64_t n_windows;   // valid k-mer windows (instances counted)
@@ -161,7 +163,11 @@ int oracle_count(const char* reads, const uint64_t* offsets, uint64_t n_reads, i
     out->hist_len = hist_len;
 
     // 1. enumerate every valid window of every read
+    // (storage only: the exact number of windows is reserved up front, so a
+    // large input holds 16 bytes per window instead of the up-to-3x of a
+    // vector grown by doubling)
     std::vector<u128> keys;
+    keys.reserve(oracle_n_windows(reads, offsets, n_reads, k));
     for (uint64_t r = 0; r < n_reads; ++r) {
         const char* s = reads + offsets[r];
         uint64_t len = offsets[r + 1] - offsets[r];

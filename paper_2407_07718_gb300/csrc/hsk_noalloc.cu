@@ -10,13 +10,16 @@
 // library holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, never a device
-// address: on the first call on each device (with that device current) the
-// entry point asks the runtime for the array's device address with
-// cudaGetSymbolAddress and keeps it.  That first call should therefore come
-// before any stream capture.  All calls share the array and it keeps the last
+// address: the first call on each device (with that device current) asks the
+// runtime for the array's device address with cudaGetSymbolAddress and keeps
+// it for the life of the process.  A cudaDeviceReset reloads the module, after
+// which that kept address is stale: do not call this entry point again after
+// resetting the device.  All calls share the array and it keeps the last
 // call's contents, so each call clears what must start at zero (histograms,
 // status words, tile counters, error word).  Two calls that overlap on the GPU
-// (different streams or host threads) race on the array.
+// (different streams or host threads) race on the array.  Every call ends by
+// reading the error word back and synchronizing its stream, so it is
+// synchronous and cannot be recorded into a CUDA graph by stream capture.
 #include <mutex>
 
 #include "../../include/hsk_stages.h"
@@ -58,9 +61,14 @@ __global__ void k_noalloc_key_base(unsigned long long* key_base, unsigned long l
 extern "C" int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words, int key_bits, void* stream) {
     if ((key_words != 1 && key_words != 2) || key_bits < 1 || key_bits > 64 * key_words || (n && !d_keys))
         return HSK_EINVAL;
+    // keys are read as whole words: 8-byte aligned, 128-bit keys 16-byte aligned
+    if (reinterpret_cast<uintptr_t>(d_keys) % (8u * (unsigned)key_words)) return HSK_EINVAL;
     const uint64_t max_n = key_words == 1 ? HSK_NOALLOC_MAX_KEYS_U64 : HSK_NOALLOC_MAX_KEYS_U128;
     if (n > max_n) return HSK_EOVERFLOW;  // beyond the fixed scratch array
     if (n <= 1) return HSK_OK;
+    // a launch error left pending by the caller's earlier work is neither
+    // cleared nor taken for this call's own: the call does nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return HSK_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return HSK_ECUDA;
     unsigned char* base = nullptr;
@@ -97,11 +105,13 @@ extern "C" int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words
     k_noalloc_key_base<<<1, 32, 0, st>>>(reinterpret_cast<unsigned long long*>(key_base), n);
     hsk::launch_digit_hist(d_keys, key_words, n, hist, P, num_sms * 4, st);
     hsk::launch_digit_offsets_seg(hist, key_base, doff, P, 1, st);
+    if (cudaGetLastError() != cudaSuccess) return HSK_ECUDA;  // a launch of this call failed
     void *src = d_keys, *dst = alt;
     for (int p = 0; p < P; ++p) {
         // the status words were zeroed above, so pass p may use epoch p + 1
         hsk::launch_onesweep_seg(src, dst, nullptr, nullptr, key_base, 1, (uint32_t)tiles, key_words, 8 * p,
                                  doff + (size_t)p * 256, status, ctr + p, (uint32_t)(p + 1), err, st);
+        if (cudaGetLastError() != cudaSuccess) return HSK_ECUDA;
         void* t = src;
         src = dst;
         dst = t;
@@ -112,7 +122,6 @@ extern "C" int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words
     int herr = 0;
     if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSK_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HSK_ECUDA;
-    if (cudaGetLastError() != cudaSuccess) return HSK_ECUDA;
     if (herr == HSK_DERR_TIMEOUT) return HSK_ETIMEOUT;
     return herr ? HSK_ECUDA : HSK_OK;
 }

@@ -1165,7 +1165,7 @@ extern "C" int hsk_stage_sort(hsk_ctx* c, uint64_t* d_keys, uint64_t n, int key_
                               void* stream) {
     return hsk_guarded(c, [&]() -> int {
         if (!c || (n && !d_keys) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
-            key_bits > 64 * key_words)
+            key_bits > 64 * key_words || reinterpret_cast<uintptr_t>(d_keys) % (8u * (unsigned)key_words))
             return HSK_EINVAL;
         CK(cudaSetDevice(c->cfg.device));
         cudaStream_t st = (cudaStream_t)stream;
@@ -1217,7 +1217,8 @@ extern "C" int hsk_stage_order(hsk_ctx* c, uint64_t* d_keys, uint32_t* d_counts,
                                int key_words, int key_bits, void* stream) {
     return hsk_guarded(c, [&]() -> int {
         if (!c || (n && (!d_keys || !d_counts)) || (key_words != 1 && key_words != 2) || key_bits < 1 ||
-            key_bits > 64 * key_words)
+            key_bits > 64 * key_words || reinterpret_cast<uintptr_t>(d_keys) % (8u * (unsigned)key_words) ||
+            reinterpret_cast<uintptr_t>(d_counts) % 4u)
             return HSK_EINVAL;
         CK(cudaSetDevice(c->cfg.device));
         cudaStream_t st = (cudaStream_t)stream;

@@ -405,7 +405,10 @@ static void launch_pass_t(const void* kin, void* kout, const uint32_t* vin, uint
 // SM always has a tile load in flight.  A copy starts at the 16-byte boundary
 // at or below the tile (so `pre` keys of the previous tile lead the buffer)
 // and covers whole 16-byte units inside the segment; a key left over at the
-// end is loaded by one thread.  Nothing is read outside the keys.
+// end is loaded by one thread.  For the first tile of a u64 key array that
+// starts 8 bytes past a 16-byte boundary the copy begins 8 bytes before the
+// array: device allocations are at least 256-byte aligned, so those bytes lie
+// in the same allocation; they are staged but never used or written.
 // Threads per CTA and keys per thread of the TMA pass (compile-time knobs);
 // CTAs per SM follow from the registers and the two staging buffers.
 #ifndef HSK_TMA_NT
