@@ -138,6 +138,13 @@ uint64_t hsk_debug_last_overflow(hsk_ctx* ctx);
  * the context stays usable. */
 int hsk_debug_wait_timeout(hsk_ctx* ctx, uint32_t spin_limit);
 
+/* Packing of the batched and served forms: *passes = packed passes run so
+ * far on this context (each counts several small jobs of one k, m and
+ * filter together), *sets = jobs they held, *alone = jobs among those that a
+ * pass could not finish (a sub-segment too large for the on-chip sort) and
+ * that were then counted alone.  NULL outputs are skipped. */
+int hsk_debug_pack_stats(hsk_ctx* ctx, uint64_t* passes, uint64_t* sets, uint64_t* alone);
+
 /* Self-check of the host block pool that holds the batched and served forms'
  * results (size classes, best-fit reuse, the cap on kept blocks, arrays
  * returning their blocks).  Host memory only: no device call is made.

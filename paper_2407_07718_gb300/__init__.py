@@ -100,6 +100,7 @@ def load():
             "hsk_profile_read": ([P, C.POINTER(d), C.POINTER(u64), i32], i32),
             "hsk_launch_count": ([], u64),
             "hsk_sort_keys_noalloc": ([P, u64, i32, i32, P], i32),
+            "hsk_debug_pack_stats": ([P, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -372,6 +373,13 @@ class Context:
         """Run a bounded device wait on a flag nothing sets; returns the code
         (HSK_ETIMEOUT expected).  See hsk_debug_wait_timeout."""
         return int(self.lib.hsk_debug_wait_timeout(self.h, spin_limit))
+
+    def pack_stats(self) -> dict:
+        """Packed passes of the batched/served forms so far: passes, jobs they
+        held, and jobs among those counted again alone."""
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        self._check(self.lib.hsk_debug_pack_stats(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"passes": a.value, "sets": b.value, "alone": c.value}
 
     def last_overflow(self) -> int:
         """Keys of the last call that went through the global radix passes

@@ -31,6 +31,11 @@ constexpr uint64_t SM_TILE_REACH = 1280;   // bases past a tile's start that its
 void launch_mark_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,
                         uint64_t* start_mask, int* err, cudaStream_t st);
 
+// packed sets: read starts of every set, padding between sets zeroed
+void launch_mark_starts_sets(const uint64_t* offsets, const uint64_t* off0, const uint64_t* n_reads,
+                             const uint64_t* base, uint32_t n_sets, uint64_t max_reads, char* reads,
+                             uint64_t* start_mask, int* err, cudaStream_t st);
+
 // ---- S2/S3 canonical k-mers, minimizers, supermers -------------------------
 enum { SM_DESC = 0, SM_DUMP = 2 };
 
@@ -42,7 +47,7 @@ struct SmParams {
     uint64_t n_packed_words, n_mask_words;
     int k, m, w;
     uint32_t seed32;
-    uint32_t n_buckets;       // a power of two
+    uint32_t n_buckets;       // a power of two (one set), or the buckets of all packed sets
     int nmax;                 // k-mers per supermer record at most
     uint32_t nmax_magic;      // ceil(2^32 / nmax): q = umulhi(x, magic) = x / nmax for x < 2^24
     int rec_words;            // 2 (k <= 32) or 4 (k <= 64)
@@ -53,6 +58,13 @@ struct SmParams {
     unsigned long long* desc_count;    // descriptors produced (may exceed desc_cap)
     uint32_t* bucket_rec;              // [n_buckets] records per bucket (atomic adds)
     uint64_t* bucket_kmers;            // [n_buckets] k-mers per bucket (atomic adds)
+    // Packed sets (n_sets > 0): set s owns warp tiles [set_tile0[s],
+    // set_tile0[s + 1]) and buckets set_bucket[s] + (score & set_bmask[s]);
+    // every set starts on a tile boundary, so a tile belongs to one set.
+    const uint32_t* set_tile0;         // n_sets + 1 entries
+    const uint32_t* set_bucket;        // n_sets entries
+    const uint32_t* set_bmask;         // n_sets entries (buckets of the set - 1)
+    uint32_t n_sets;
     uint8_t* dump_valid;               // (DUMP)
     uint64_t* dump_key;
     uint64_t* dump_minhash;
@@ -92,12 +104,21 @@ void launch_expand_seg(const uint64_t* records, const uint64_t* rec_base, const 
 // Digit histograms of plain keys (one segment): hist[p][256].
 void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hist, int n_pass,
                        int grid, cudaStream_t st);
+// Digit histograms of C consecutive segments of plain keys (keys
+// [key_base[c], key_base[c+1]) of n): hist[c][p][256], accumulated.
+void launch_digit_hist_seg(const void* keys, int key_words, const uint64_t* key_base, uint32_t C, uint64_t n,
+                           uint64_t* hist, int n_pass, cudaStream_t st);
+// dst[i] = src[idx[i]] for i < n
+void launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint32_t n, uint64_t* dst, cudaStream_t st);
 // doff[p][c][d] = key_base[c] + exclusive prefix over d of hist[c][p][d]
 void launch_digit_offsets_seg(const uint64_t* hist, const uint64_t* key_base, uint64_t* doff, int n_pass,
                               uint32_t C, cudaStream_t st);
 
-// One LSD pass over C segments (tmax = most tiles of any segment), optionally
-// carrying uint32 values; status: C * tmax * 256 words; doff: this pass's [C][256].
+// One LSD pass over C segments, optionally carrying uint32 values; doff: this
+// pass's [C][256].  Interleaved segments (tile_start == nullptr): tmax = most
+// tiles of any segment, status C * tmax * 256 words.  Listed segments:
+// segment c owns global tiles [tile_start[c], tile_start[c + 1]), tmax = all
+// tiles (tile_start[C]), status tmax * 256 words.
 uint64_t onesweep_tile_keys(int key_words);
 // S6: counts into / out of the keys' bits from cshift up (cshift = 8 * passes)
 void launch_pack_pairs(void* keys, uint32_t* counts, uint64_t n, int key_words, int cshift, bool unpack, int grid,
@@ -105,9 +126,9 @@ void launch_pack_pairs(void* keys, uint32_t* counts, uint64_t n, int key_words, 
 // status: >= 2 * LB_PAD zeroed words
 void launch_debug_wait(uint64_t* status, uint32_t spin_limit, int* err, cudaStream_t st);
 void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
-                         const uint64_t* key_base, uint32_t C, uint32_t tmax, int key_words, int shift,
-                         const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err,
-                         cudaStream_t st);
+                         const uint64_t* key_base, uint32_t C, uint32_t tmax, const uint32_t* tile_start,
+                         int key_words, int shift, const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr,
+                         uint32_t epoch, int* err, cudaStream_t st);
 
 // ---- S5 run-length count, filter, histogram -------------------------------
 // on-chip sort of sub-segments (k_local.cu)
@@ -118,11 +139,13 @@ void launch_part(int mode, const uint64_t* records, const uint64_t* rec_base, co
                  cudaStream_t st);
 uint32_t local_cap(int key_words);
 uint32_t local_cap_big(int key_words);
+// grp_set: set of each group (packed sets; nullptr = one set), statistics
+// per set at hist + set * hist_len, max_count[set], n_distinct[set]
 void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, bool big, int shift0,
                        int key_words, void* keys, uint32_t* kcount, uint32_t* kc, uint32_t* ov_list,
                        uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
-                       uint32_t* max_count, uint64_t* n_distinct, uint32_t* claim, int* err, int num_sms,
-                       cudaStream_t st);
+                       uint32_t* max_count, uint64_t* n_distinct, const uint32_t* grp_set, uint32_t* claim,
+                       int* err, int num_sms, cudaStream_t st);
 void launch_compact(const uint64_t* sub_off, const uint32_t* kc, const uint64_t* out_off, uint32_t n_sub,
                     int key_words, const void* keys, const uint32_t* kcount, void* out_keys, uint32_t* out_counts,
                     uint64_t out_cap, int* err, int grid, cudaStream_t st);

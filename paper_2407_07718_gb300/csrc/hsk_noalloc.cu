@@ -109,7 +109,7 @@ extern "C" int hsk_sort_keys_noalloc(uint64_t* d_keys, uint64_t n, int key_words
     void *src = d_keys, *dst = alt;
     for (int p = 0; p < P; ++p) {
         // the status words were zeroed above, so pass p may use epoch p + 1
-        hsk::launch_onesweep_seg(src, dst, nullptr, nullptr, key_base, 1, (uint32_t)tiles, key_words, 8 * p,
+        hsk::launch_onesweep_seg(src, dst, nullptr, nullptr, key_base, 1, (uint32_t)tiles, nullptr, key_words, 8 * p,
                                  doff + (size_t)p * 256, status, ctr + p, (uint32_t)(p + 1), err, st);
         if (cudaGetLastError() != cudaSuccess) return HSK_ECUDA;
         void* t = src;

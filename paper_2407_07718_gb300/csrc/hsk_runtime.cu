@@ -124,7 +124,7 @@ int hsk_next_counter(hsk_ctx* c, cudaStream_t st, uint32_t** ctr) {
 
 // Grow the shared look-back status buffer (new memory is zeroed: stale bytes
 // could otherwise look like a status word of the current epoch).
-static int ensure_status(hsk_ctx* c, uint64_t words, cudaStream_t st) {
+int hsk_ensure_status(hsk_ctx* c, uint64_t words, cudaStream_t st) {
     if (c->lb_status.cap >= words * 8) return HSK_OK;
     CK(cudaStreamSynchronize(st));
     return hsk_ensure(c, c->lb_status, words * 8, true);
@@ -308,7 +308,7 @@ static int check_args(hsk_ctx* c, const void* reads, const void* offsets, uint64
 
 // Reads the device error word (and the largest count, stored 8 bytes after it)
 // once the stream's work is done.
-static int read_device_error(hsk_ctx* c, cudaStream_t st, uint32_t* max_count = nullptr) {
+int hsk_read_device_error(hsk_ctx* c, cudaStream_t st, uint32_t* max_count) {
     uint32_t w[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(w, c->d_err, sizeof(w), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -384,10 +384,17 @@ static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t 
 }
 
 // Count supermers per (bucket, CTA), scan to record offsets, scatter records.
-int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S,
-                  cudaStream_t st, InputPipe* pipe) {
+// With a set map the bases hold packed sets and B is the buckets of all sets.
+int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S, cudaStream_t st,
+                  InputPipe* pipe, const SetMap* sets) {
     SmParams P;
     fill_sm_params(c, E, k, m, B, P);
+    if (sets) {
+        P.set_tile0 = sets->tile0;
+        P.set_bucket = sets->bucket;
+        P.set_bmask = sets->bmask;
+        P.n_sets = sets->n;
+    }
     const bool wide = k > 32;
     const int nreg = P.w <= 33 ? 2 : 3;
     const int occ = supermer_max_ctas_per_sm(SM_DESC, wide, nreg, B);
@@ -453,7 +460,7 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
         cap = n_desc;  // the walk counted every supermer: one more run fits them all
     }
     // record offsets of the buckets
-    TRY(ensure_status(c, scan_status_words(B), st));
+    TRY(hsk_ensure_status(c, scan_status_words(B), st));
     uint32_t ep, *ctr;
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
@@ -465,7 +472,7 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
     S.h_bucket_rec.resize((size_t)B + 1);
     CK(cudaMemcpyAsync(S.h_bucket_kmers.data(), c->bucket_kmers.p, (size_t)B * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(S.h_bucket_rec.data(), c->bucket_rec.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, st));
-    TRY(read_device_error(c, st));
+    TRY(hsk_read_device_error(c, st));
     S.n_records = S.h_bucket_rec[B];
     if (S.n_records != n_desc) {
         hsk_set_error(c, "supermer count mismatch: %llu descriptors, %llu records",
@@ -488,7 +495,7 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
 static int n_passes_for(int key_bits) { return (key_bits + 7) / 8; }
 
 // Output capacity for `need` pairs; the pairs already there are kept.
-static int grow_output(hsk_ctx* c, const Output& O, uint64_t need, int key_words, cudaStream_t st) {
+int hsk_grow_output(hsk_ctx* c, const Output& O, uint64_t need, int key_words, cudaStream_t st) {
     const size_t kb = (size_t)key_words * 8;
     if (c->out_keys.cap >= need * kb && c->out_counts.cap >= need * 4) return HSK_OK;
     DevBuf nk, ncn;
@@ -507,7 +514,7 @@ static int grow_output(hsk_ctx* c, const Output& O, uint64_t need, int key_words
 }
 
 // C zeroed tile counters in a row for one launch.
-static int next_counters(hsk_ctx* c, cudaStream_t st, uint32_t n, uint32_t** ctr) {
+int hsk_next_counters(hsk_ctx* c, cudaStream_t st, uint32_t n, uint32_t** ctr) {
     if (n > HSK_N_COUNTERS) {
         hsk_set_error(c, "%u tile counters requested", n);
         return HSK_EINVAL;
@@ -523,7 +530,7 @@ static int next_counters(hsk_ctx* c, cudaStream_t st, uint32_t n, uint32_t** ctr
 
 // Segment boundaries (C + 1 key offsets, and record offsets when given) to
 // the device; the host arrays are copied before the call returns.
-static int upload_segments(hsk_ctx* c, const std::vector<uint64_t>& key_base,
+int hsk_upload_segments(hsk_ctx* c, const std::vector<uint64_t>& key_base,
                            const std::vector<uint64_t>* rec_base, cudaStream_t st) {
     size_t n = key_base.size();
     TRY(hsk_ensure(c, c->seg, 2 * n * 8, false));
@@ -541,14 +548,14 @@ static int sort_segments(hsk_ctx* c, void* a, void* b, uint32_t* va, uint32_t* v
                          bool* sorted_in_b, cudaStream_t st) {
     *sorted_in_b = false;
     if (tmax == 0 || n_pass == 0) return HSK_OK;
-    TRY(ensure_status(c, (uint64_t)C * tmax * 256 + 1, st));
+    TRY(hsk_ensure_status(c, (uint64_t)C * tmax * 256 + 1, st));
     void *src = a, *dst = b;
     uint32_t *vs = va, *vd = vb;
     for (int p = 0; p < n_pass; ++p) {
         uint32_t ep, *ctr;
         TRY(hsk_next_epoch(c, st, &ep));
         TRY(hsk_next_counter(c, st, &ctr));
-        launch_onesweep_seg(src, dst, vs, vd, d_key_base, C, tmax, key_words, 8 * p, doff + (size_t)p * C * 256,
+        launch_onesweep_seg(src, dst, vs, vd, d_key_base, C, tmax, nullptr, key_words, 8 * p, doff + (size_t)p * C * 256,
                             (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
         std::swap(src, dst);
         std::swap(vs, vd);
@@ -569,7 +576,7 @@ static int plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int ke
     TRY(hsk_ensure(c, c->pass_hist, 16 * 256 * 8, false));
     TRY(hsk_ensure(c, c->digit_off, 16 * 256 * 8, false));
     std::vector<uint64_t> kb0 = {0, n};
-    TRY(upload_segments(c, kb0, nullptr, st));
+    TRY(hsk_upload_segments(c, kb0, nullptr, st));
     CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)P * 256 * 8, st));
     launch_digit_hist(keys, key_words, n, (uint64_t*)c->pass_hist.p, P, c->num_sms * 4, st);
     launch_digit_offsets_seg((uint64_t*)c->pass_hist.p, (const uint64_t*)c->seg.p, (uint64_t*)c->digit_off.p, P,
@@ -608,7 +615,7 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
     launch_rle_mark(sorted, n, key_words, (uint32_t*)c->heads.p, t_first, t_last, t_keep, lo, hi, d_hist,
                     hist_len, c->d_max, c->d_nheads, c->num_sms * (key_words == 1 ? 4 : 2), st);
     launch_rle_close(t_first, t_last, t_next, b_min, nt, n, t_keep, lo, hi, d_hist, hist_len, c->d_max, st);
-    TRY(ensure_status(c, scan_status_words(nt), st));
+    TRY(hsk_ensure_status(c, scan_status_words(nt), st));
     uint32_t ep, *ctr;
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
@@ -620,7 +627,7 @@ int hsk_rle_chunk(hsk_ctx* c, const void* sorted, uint64_t n, int key_words, uin
     CK(cudaStreamSynchronize(st));
     O.n_distinct += D;
     const size_t kb = (size_t)key_words * 8;
-    TRY(grow_output(c, O, O.n_pairs + kept, key_words, st));
+    TRY(hsk_grow_output(c, O, O.n_pairs + kept, key_words, st));
     launch_rle_write(sorted, n, key_words, (const uint32_t*)c->heads.p, t_next, t_off, lo, hi,
                      (char*)c->out_keys.p + O.n_pairs * kb, (uint32_t*)c->out_counts.p + O.n_pairs, kept,
                      c->d_err, c->num_sms * 4, st);
@@ -650,7 +657,7 @@ int hsk_order_pairs(hsk_ctx* c, void* keys, uint32_t* counts, uint64_t n, int ke
 
 // Split buckets [b0, b1) into at most C_want groups of roughly equal k-mer
 // counts; returns the first bucket of every group and b1.
-static std::vector<uint32_t> group_buckets(const Supermers& S, uint32_t b0, uint32_t b1, uint32_t C_want) {
+std::vector<uint32_t> hsk_group_buckets(const Supermers& S, uint32_t b0, uint32_t b1, uint32_t C_want) {
     uint64_t total = 0;
     for (uint32_t b = b0; b < b1; ++b) total += S.h_bucket_kmers[b];
     std::vector<uint32_t> cut = {b0};
@@ -744,7 +751,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     uint64_t* cursor = sub_off + NS + 1;
     uint64_t* kc_off = cursor + NS;
     TRY(hsk_ensure(c, c->batch_d, std::max<uint64_t>(nt, 1) * 4, false));
-    TRY(upload_segments(c, rbase, &tbase, st));
+    TRY(hsk_upload_segments(c, rbase, &tbase, st));
     if (nt) CK(cudaMemcpyAsync(c->batch_d.p, tseg.data(), nt * 4, cudaMemcpyHostToDevice, st));
     const uint64_t* d_rbase = (const uint64_t*)c->seg.p;
     const uint64_t* d_tbase = d_rbase + (C + 1);
@@ -755,7 +762,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     TRY(hsk_next_counter(c, st, &ctr));
     launch_part(0, S.records, d_rbase, d_tbase, d_tseg, (uint32_t)nt, k, shift0, ctr, sub_cnt, nullptr, nullptr,
                 nullptr, c->d_err, expand_grid(c->num_sms), st);
-    TRY(ensure_status(c, scan_status_words(NS), st));
+    TRY(hsk_ensure_status(c, scan_status_words(NS), st));
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
     launch_scan_u32(sub_cnt, NS, sub_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
@@ -771,7 +778,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     CK(cudaMemsetAsync(c->d_nlocal, 0, 40, st));  // distinct, pass-1 and pass-2 overflow stats
     TRY(hsk_next_counter(c, st, &ctr));
     launch_local_sort(sub_off, nullptr, (uint32_t)NS, false, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
-                      ov_list, c->d_ovstats, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, ctr, c->d_err,
+                      ov_list, c->d_ovstats, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, nullptr, ctr, c->d_err,
                       c->num_sms, st);
     CK(cudaGetLastError());
     uint64_t st5[5] = {0, 0, 0, 0, 0};  // distinct, pass-1 {listed, keys}, pass-2 {listed, keys}
@@ -781,7 +788,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     if (n_ov1) {
         TRY(hsk_next_counter(c, st, &ctr));
         launch_local_sort(sub_off, ov_list, n_ov1, true, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
-                          ov_list2, c->d_ovstats + 2, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, ctr,
+                          ov_list2, c->d_ovstats + 2, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, nullptr, ctr,
                           c->d_err, c->num_sms, st);
         CK(cudaGetLastError());
     }
@@ -797,7 +804,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     const uint32_t n_ov = (uint32_t)(st5[3] & 0xFFFFFFFFull);
     const uint64_t ov_keys = st5[4];
     O.n_distinct += st5[0];
-    TRY(grow_output(c, O, O.n_pairs + kept, kw, st));
+    TRY(hsk_grow_output(c, O, O.n_pairs + kept, kw, st));
     launch_compact(sub_off, kcv, kc_off, (uint32_t)NS, kw, c->keys.p, (const uint32_t*)c->alt.p,
                    (char*)c->out_keys.p + O.n_pairs * kb, (uint32_t*)c->out_counts.p + O.n_pairs, kept, c->d_err,
                    c->num_sms * 8, st);
@@ -869,7 +876,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
             const uint32_t C_want = (uint32_t)std::min<uint64_t>(ch.second - ch.first,
                                                                  std::max<uint64_t>(1, nk / per_group));
             NvtxRange r("S4-S5 on-chip sort and count");
-            TRY(local_chunk(c, S, group_buckets(S, ch.first, ch.second, C_want), nk, k, lo, hi, H, O, st));
+            TRY(local_chunk(c, S, hsk_group_buckets(S, ch.first, ch.second, C_want), nk, k, lo, hi, H, O, st));
             unordered = true;
             continue;
         }
@@ -877,7 +884,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
         NvtxRange r("S4-S5 global radix sort and count");
         uint32_t C_want = (uint32_t)std::min<uint64_t>({(uint64_t)HSK_SEGMENTS, ch.second - ch.first,
                                                         std::max<uint64_t>(1, nk / HSK_MIN_SEGMENT_KMERS)});
-        std::vector<uint32_t> cut = group_buckets(S, ch.first, ch.second, C_want);
+        std::vector<uint32_t> cut = hsk_group_buckets(S, ch.first, ch.second, C_want);
         const uint32_t C = (uint32_t)cut.size() - 1;
         total_segments += C;
         std::vector<uint64_t> kbase(C + 1), rbase(C + 1);
@@ -898,14 +905,14 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
         TRY(hsk_ensure(c, c->alt, nk * kb, false));
         TRY(hsk_ensure(c, c->pass_hist, (size_t)C * P * 256 * 8, false));
         TRY(hsk_ensure(c, c->digit_off, (size_t)C * P * 256 * 8, false));
-        TRY(ensure_status(c, (uint64_t)C * (max_rt + 1) * 4 + 4, st));
-        TRY(upload_segments(c, kbase, &rbase, st));
+        TRY(hsk_ensure_status(c, (uint64_t)C * (max_rt + 1) * 4 + 4, st));
+        TRY(hsk_upload_segments(c, kbase, &rbase, st));
         const uint64_t* d_kbase = (const uint64_t*)c->seg.p;
         const uint64_t* d_rbase = d_kbase + (C + 1);
         CK(cudaMemsetAsync(c->pass_hist.p, 0, (size_t)C * P * 256 * 8, st));
         uint32_t ep, *ctrs;
         TRY(hsk_next_epoch(c, st, &ep));
-        TRY(next_counters(c, st, C, &ctrs));
+        TRY(hsk_next_counters(c, st, C, &ctrs));
         launch_expand_seg(S.records, d_rbase, d_kbase, C, max_rt, k, c->keys.p, (uint64_t*)c->lb_status.p, ctrs,
                           ep, (uint64_t*)c->pass_hist.p, P, c->d_err, expand_grid(c->num_sms), st);
         launch_digit_offsets_seg((uint64_t*)c->pass_hist.p, d_kbase, (uint64_t*)c->digit_off.p, P, C, st);
@@ -927,7 +934,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     prof_mark(c, st, 6);
     CK(cudaEventRecord(c->ev1, st));
     uint32_t mx = 0;
-    TRY(read_device_error(c, st, &mx));
+    TRY(hsk_read_device_error(c, st, &mx));
     prof_collect(c);
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
@@ -1102,7 +1109,7 @@ extern "C" int hsk_stage_encode(hsk_ctx* c, const char* d_reads, uint64_t n_base
         launch_mark_starts(d_offsets, n_reads, n_bases, d_start, c->d_err, st);
         launch_encode(d_reads, n_bases, d_packed, d_invalid, n_pw, n_mw, st);
         CK(cudaGetLastError());
-        return read_device_error(c, st);
+        return hsk_read_device_error(c, st);
     });
 }
 
@@ -1126,7 +1133,7 @@ extern "C" int hsk_stage_windows(hsk_ctx* c, const char* d_reads, const uint64_t
         P.dump_minhash = d_minhash;
         launch_supermer(SM_DUMP, P, st);
         CK(cudaGetLastError());
-        return read_device_error(c, st);
+        return hsk_read_device_error(c, st);
     });
 }
 
@@ -1157,7 +1164,7 @@ extern "C" int hsk_stage_supermers(hsk_ctx* c, const char* d_reads, const uint64
         *n_records = S.n_records;
         *record_words = S.rec_words;
         if (max_kmers) *max_kmers = S.nmax;
-        return read_device_error(c, st);
+        return hsk_read_device_error(c, st);
     });
 }
 
@@ -1175,7 +1182,7 @@ extern "C" int hsk_stage_sort(hsk_ctx* c, uint64_t* d_keys, uint64_t n, int key_
         c->ctr_used = 0;
         if (n <= 1) return HSK_OK;
         TRY(plain_sort(c, d_keys, nullptr, n, key_words, key_bits, c->alt, nullptr, st));
-        return read_device_error(c, st);
+        return hsk_read_device_error(c, st);
     });
 }
 
@@ -1195,7 +1202,7 @@ extern "C" int hsk_stage_rle(hsk_ctx* c, const uint64_t* d_sorted, uint64_t n, i
         Output O;
         TRY(hsk_rle_chunk(c, d_sorted, n, key_words, lo, hi, H, (uint64_t*)c->hist.p, O, st));
         uint32_t mx = 0;
-        TRY(read_device_error(c, st, &mx));
+        TRY(hsk_read_device_error(c, st, &mx));
         DevResult R;
         memset(&R, 0, sizeof R);
         R.n_pairs = O.n_pairs;
@@ -1227,7 +1234,7 @@ extern "C" int hsk_stage_order(hsk_ctx* c, uint64_t* d_keys, uint32_t* d_counts,
         CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
         c->ctr_used = 0;
         TRY(hsk_order_pairs(c, d_keys, d_counts, n, key_words, key_bits, st, 0));
-        return read_device_error(c, st);
+        return hsk_read_device_error(c, st);
     });
 }
 
@@ -1241,7 +1248,7 @@ extern "C" int hsk_debug_wait_timeout(hsk_ctx* c, uint32_t spin_limit) {
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     launch_debug_wait((uint64_t*)c->batch_c.p, spin_limit, c->d_err, st);
     CK(cudaGetLastError());
-    const int rc = read_device_error(c, st);
+    const int rc = hsk_read_device_error(c, st);
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     CK(cudaStreamSynchronize(st));
     return rc;

@@ -284,6 +284,15 @@ struct hsk_ctx {
     DevBuf pair_alt_keys, pair_alt_counts;                         // S6
     DevBuf loc_tab;                                                // on-chip path: sub-segment tables
     DevBuf batch_a, batch_b, batch_c, batch_d;                     // on-chip path: overflow keys, tile map
+    DevBuf pack_tab, pack_stat;                                    // packed sets: set tables, per-set statistics
+
+    // tuned parameters (0 = built-in default); see hsk_tune.cu
+    struct Tune {
+        uint32_t group_div = 0;        // bucket-group keys = 256 x on-chip capacity / group_div
+        uint64_t pack_bases = 0;       // bases of one pack at most
+        uint64_t pack_small = 0;       // sets with more bases run alone
+        int slots = 0;                 // serving slots
+    } tune;
 
     void* h_pin = nullptr;
     size_t h_pin_cap = 0;
@@ -293,6 +302,9 @@ struct hsk_ctx {
     std::vector<HostResult> batch_res;   // results of the last hsk_count_batch
 
     ServeState* serve = nullptr;
+    // packed passes run for this context's batched and served jobs, the sets
+    // they held, and the sets among them counted again alone
+    std::atomic<uint64_t> pack_passes{0}, pack_sets{0}, pack_redo{0};
 
     // profiling: events at stage boundaries (stage id of the span that ends there)
     bool prof = false;
@@ -306,8 +318,17 @@ struct hsk_ctx {
         return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
                 &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads, &rle_tiles,
                 &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &loc_tab, &batch_a,
-                &batch_b, &batch_c, &batch_d};
+                &batch_b, &batch_c, &batch_d, &pack_tab, &pack_stat};
     }
+};
+
+// Packed sets of one pass (device arrays; see SmParams): set s owns warp
+// tiles [tile0[s], tile0[s + 1]) and buckets bucket[s] .. bucket[s] + bmask[s].
+struct SetMap {
+    const uint32_t* tile0 = nullptr;
+    const uint32_t* bucket = nullptr;
+    const uint32_t* bmask = nullptr;
+    uint32_t n = 0;
 };
 
 void hsk_set_error(hsk_ctx* c, const char* fmt, ...);
@@ -357,6 +378,19 @@ int hsk_guarded(hsk_ctx* c, F&& body) {
     }
 }
 int hsk_ensure(hsk_ctx* c, DevBuf& b, size_t bytes, bool zero_new);
+int hsk_ensure_status(hsk_ctx* c, uint64_t words, cudaStream_t st);
+int hsk_next_epoch(hsk_ctx* c, cudaStream_t st, uint32_t* epoch);
+int hsk_next_counter(hsk_ctx* c, cudaStream_t st, uint32_t** ctr);
+int hsk_next_counters(hsk_ctx* c, cudaStream_t st, uint32_t n, uint32_t** ctr);
+int hsk_read_device_error(hsk_ctx* c, cudaStream_t st, uint32_t* max_count = nullptr);
+int hsk_upload_segments(hsk_ctx* c, const std::vector<uint64_t>& key_base, const std::vector<uint64_t>* rec_base,
+                        cudaStream_t st);
+int hsk_grow_output(hsk_ctx* c, const Output& O, uint64_t need, int key_words, cudaStream_t st);
+std::vector<uint32_t> hsk_group_buckets(const Supermers& S, uint32_t b0, uint32_t b1, uint32_t C_want);
+int hsk_plan_chunks(hsk_ctx* c, const Supermers& S, int key_words, std::vector<std::pair<uint32_t, uint32_t>>& chunks);
+int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S, cudaStream_t st,
+                  InputPipe* pipe, const SetMap* sets = nullptr);
+uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k);
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
                   DevResult& R, InputPipe* pipe = nullptr);

@@ -8,14 +8,22 @@
 // budget next to what the other slots hold; idle slots give their arenas back
 // when a job would not fit otherwise.  Jobs complete in any order.
 //
+// Small jobs are batched at the kernel level: a slot that takes a small job
+// also takes the other queued small jobs with the same k, m and filter (up to
+// a pack size, and within the budget) and counts them all by one pass of the
+// pipeline (hsk_pack.cu), so they share every launch and synchronization.
+// Jobs that arrive while a pack runs wait for the next free slot.
+//
 // Batched form: hsk_count_batch queues many independent read sets on the same
-// slots, largest first, and returns when all are done.
+// slots, largest first, and returns when all are done; the small sets are
+// packed as above.
 #include <algorithm>
 #include <cstdlib>
 #include <chrono>
 #include <cstring>
 
 #include "hsk_internal.h"
+#include "hsk_pack.h"
 #include "hsk_runtime.h"
 
 namespace {
@@ -33,6 +41,8 @@ struct Ticket {
     std::string err;
     HostResult res;
     size_t est = 0;
+    uint64_t bases = 0;
+    bool packable = false;  // small enough to share a pass with other jobs
     double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -62,6 +72,32 @@ static size_t job_estimate(const hsk_job& j) {
     double bytes = n * (1.0 + 0.25 + 0.25) + 8.0 * (double)(j.n_reads + 1) + n * rec / 2.0 +
                    n * (2 * kb + 4 + 1 + kb + 4) + (96u << 20);
     return (size_t)bytes;
+}
+
+// Pack limits (the tuned values when set): sets of more bases run alone;
+// a pack holds at most pack_bases bases.
+static uint64_t pack_small_limit(const hsk_ctx* c) {
+    return c->tune.pack_small ? c->tune.pack_small : (256ull << 20);
+}
+static uint64_t pack_bases_limit(const hsk_ctx* c) {
+    return c->tune.pack_bases ? c->tune.pack_bases : (1ull << 30);
+}
+constexpr uint32_t PACK_MAX_SETS = 1024;
+
+// Device bytes of a pack of S sets holding `bases` bases and `reads` reads.
+static size_t pack_estimate(uint64_t bases, uint64_t reads, int k, uint32_t S, uint32_t hist_len) {
+    hsk_job j{};
+    j.k = k;
+    uint64_t off[2] = {0, bases};
+    j.offsets = off;
+    j.n_reads = 1;
+    size_t e = job_estimate(j) + (size_t)8 * (reads + S) + (size_t)S * hist_len * 8 +
+               (size_t)S * 1024 * 8;  // inputs and offsets, per-set histograms, set padding
+    return e;
+}
+
+static bool same_class(const hsk_job& a, const hsk_job& b) {
+    return a.k == b.k && a.m == b.m && a.lo == b.lo && a.hi == b.hi;
 }
 
 static size_t slot_held(ServeState* S, int i) {
@@ -116,28 +152,97 @@ static void worker_main(hsk_ctx* parent, ServeState* S, int slot) {
             }
             S->cv_work.wait(lk);
         }
-        T->state = T_RUNNING;
-        T->t_start = now_s();
+        // small job: other queued small jobs of its class join it in one pass
+        std::vector<Ticket*> group{T};
+        size_t est = T->est;
+        if (T->packable) {
+            uint64_t queued = T->bases;
+            for (uint64_t id : S->queue) {
+                Ticket* u = S->tickets[id].get();
+                if (u->packable && same_class(u->job, T->job)) queued += u->bases;
+            }
+            // spread the queued small work over the slots, within the pack limit
+            const uint64_t cap = std::min<uint64_t>(pack_bases_limit(parent),
+                                                    std::max<uint64_t>(32ull << 20, queued / S->slots.size()));
+            uint64_t bases = T->bases, reads = T->job.n_reads;
+            const int kw = T->job.k <= 32 ? 1 : 2;
+            const uint64_t gk = hsk_pack_group_keys(c, kw);
+            uint32_t buckets = hsk_pack_set_buckets(T->bases, kw, gk);
+            size_t others = 0;
+            for (int i = 0; i < (int)S->slots.size(); ++i)
+                if (i != slot) others += slot_held(S, i);
+            for (auto it = S->queue.begin(); it != S->queue.end() && bases < cap && group.size() < PACK_MAX_SETS;) {
+                Ticket* u = S->tickets[*it].get();
+                const uint32_t ub = hsk_pack_set_buckets(u->bases, kw, gk);
+                if (u->packable && same_class(u->job, T->job) && bases + u->bases <= cap &&
+                    buckets + ub <= HSK_MAX_BUCKETS) {
+                    const size_t e2 = pack_estimate(bases + u->bases, reads + u->job.n_reads, T->job.k,
+                                                    (uint32_t)group.size() + 1, parent->cfg.hist_len);
+                    if (others + std::max(c->allocated, e2) <= S->budget) {
+                        group.push_back(u);
+                        bases += u->bases;
+                        reads += u->job.n_reads;
+                        buckets += ub;
+                        est = e2;
+                        it = S->queue.erase(it);
+                        continue;
+                    }
+                }
+                ++it;
+            }
+        }
+        const double t0 = now_s();
+        for (Ticket* g : group) {
+            g->state = T_RUNNING;
+            g->t_start = t0;
+        }
         S->slot_busy[slot] = 1;
-        S->slot_est[slot] = T->est;
-        hsk_job job = T->job;
+        S->slot_est[slot] = est;
         lk.unlock();
-        HostResult hr;
-        hr.set_pool(&parent->result_pool);
-        int rc = hsk_guarded(c, [&]() -> int {
-            return hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo, job.hi,
-                                     c->stream, c->in_reads, c->in_offsets, hr);
-        });
-        std::string err = rc == HSK_OK ? std::string() : c->err_msg;
+        std::vector<HostResult> hrs(group.size());
+        for (HostResult& h : hrs) h.set_pool(&parent->result_pool);
+        std::vector<int> rcs(group.size(), HSK_OK);
+        std::vector<std::string> errs(group.size());
+        if (group.size() == 1) {
+            const hsk_job job = group[0]->job;
+            rcs[0] = hsk_guarded(c, [&]() -> int {
+                return hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo, job.hi,
+                                         c->stream, c->in_reads, c->in_offsets, hrs[0]);
+            });
+            if (rcs[0] != HSK_OK) errs[0] = c->err_msg;
+        } else {
+            std::vector<PackSet> ps(group.size());
+            for (size_t i = 0; i < group.size(); ++i) {
+                ps[i].reads = group[i]->job.reads;
+                ps[i].offsets = group[i]->job.offsets;
+                ps[i].n_reads = group[i]->job.n_reads;
+                ps[i].out = &hrs[i];
+            }
+            const hsk_job& j0 = group[0]->job;
+            const int rc = hsk_guarded(c, [&]() -> int {
+                return hsk_count_pack_host(c, ps.data(), (uint32_t)ps.size(), j0.k, j0.m, j0.lo, j0.hi, c->stream);
+            });
+            for (size_t i = 0; i < group.size(); ++i) {
+                rcs[i] = rc != HSK_OK ? rc : ps[i].rc;
+                errs[i] = rc != HSK_OK ? c->err_msg : ps[i].err;
+                if (ps[i].alone) parent->pack_redo.fetch_add(1);
+            }
+            parent->pack_passes.fetch_add(1);
+            parent->pack_sets.fetch_add(group.size());
+        }
         lk.lock();
-        T->rc = rc;
-        T->err = err;
-        T->res = std::move(hr);
-        T->res.R.kmers = T->res.kmers.data();
-        T->res.R.counts = T->res.counts.data();
-        T->res.R.hist = T->res.hist.data();
-        T->t_done = now_s();
-        T->state = T_DONE;
+        const double t1 = now_s();
+        for (size_t i = 0; i < group.size(); ++i) {
+            Ticket* g = group[i];
+            g->rc = rcs[i];
+            g->err = rcs[i] == HSK_OK ? std::string() : errs[i];
+            g->res = std::move(hrs[i]);
+            g->res.R.kmers = g->res.kmers.data();
+            g->res.R.counts = g->res.counts.data();
+            g->res.R.hist = g->res.hist.data();
+            g->t_done = t1;
+            g->state = T_DONE;
+        }
         S->slot_busy[slot] = 0;
         S->slot_est[slot] = 0;
         S->cv_done.notify_all();
@@ -150,7 +255,7 @@ static int serve_start(hsk_ctx* c) {
     ServeState* S = new ServeState();
     S->budget = c->budget > c->allocated ? c->budget - c->allocated : 0;
     // slots (child contexts running jobs side by side); HSK_SERVE_SLOTS overrides
-    int n_slots = 4;
+    int n_slots = c->tune.slots ? c->tune.slots : 4;
     if (const char* e = getenv("HSK_SERVE_SLOTS")) {
         const int v = atoi(e);
         if (v >= 1 && v <= 32) n_slots = v;
@@ -166,6 +271,7 @@ static int serve_start(hsk_ctx* c) {
             hsk_set_error(c, "could not create serving slot %d", i);
             return rc;
         }
+        child->tune = c->tune;
         S->slots.push_back(child);
         S->slot_est.push_back(0);
         S->slot_busy.push_back(0);
@@ -217,6 +323,8 @@ extern "C" int hsk_submit(hsk_ctx* c, const hsk_job* job, uint64_t* ticket) {
         auto T = std::make_unique<Ticket>();
         T->job = *job;
         T->est = job_estimate(*job);
+        T->bases = job->n_reads ? job->offsets[job->n_reads] : 0;
+        T->packable = T->bases <= pack_small_limit(c);
         T->t_submit = now_s();
         std::lock_guard<std::mutex> g(S->mu);
         uint64_t id = S->next_ticket++;
@@ -345,6 +453,8 @@ extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs,
                 auto T = std::make_unique<Ticket>();
                 T->job = jobs[i];
                 T->est = job_estimate(jobs[i]);
+                T->bases = bases(i);
+                T->packable = T->bases <= pack_small_limit(c);
                 T->t_submit = now_s();
                 uint64_t id = S->next_ticket++;
                 S->tickets[id] = std::move(T);
@@ -375,4 +485,12 @@ extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs,
         for (uint32_t i = 0; i < n_jobs; ++i) fill_out(c->batch_res[i], outs + i);
         return HSK_OK;
     });
+}
+
+extern "C" int hsk_debug_pack_stats(hsk_ctx* c, uint64_t* passes, uint64_t* sets, uint64_t* alone) {
+    if (!c) return HSK_EINVAL;
+    if (passes) *passes = c->pack_passes.load();
+    if (sets) *sets = c->pack_sets.load();
+    if (alone) *alone = c->pack_redo.load();
+    return HSK_OK;
 }

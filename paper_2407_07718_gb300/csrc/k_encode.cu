@@ -81,6 +81,47 @@ __global__ void k_mark_starts(const uint64_t* __restrict__ offsets, uint64_t n_r
     if (e > s) atomicOr(start + (s >> 6), 1ULL << (63 - (s & 63)));
 }
 
+// Packed sets: set y's reads are offsets[off0[y] .. off0[y] + n_reads[y]]
+// (its own offsets, starting at 0) placed at base[y] of the packed bases;
+// the bytes from the set's last base to base[y + 1] are padding and are set
+// to 0 here (an invalid byte, so no window reaches into them).  Marks the first
+// base of every non-empty read; offsets that leave the set's range are an
+// error.
+__global__ void k_mark_starts_sets(const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ off0,
+                                   const uint64_t* __restrict__ n_reads, const uint64_t* __restrict__ base,
+                                   char* reads, u64* __restrict__ start, int* err) {
+    const uint32_t y = blockIdx.y;
+    const uint64_t nr = n_reads[y], b0 = base[y], b1 = base[y + 1];
+    const uint64_t* o = offsets + off0[y];
+    const uint64_t nb = o[nr];
+    if (o[0] != 0 || b0 + nb > b1) {  // every block checks: nothing is written outside the set
+        if (blockIdx.x == 0 && threadIdx.x == 0) raise_error(err, HSK_DERR_OFFSETS);
+        return;
+    }
+    if (blockIdx.x == 0)
+        for (uint64_t p = b0 + nb + threadIdx.x; p < b1; p += blockDim.x) reads[p] = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = o[i], e = o[i + 1];
+        if (e < a || e > nb) {
+            raise_error(err, HSK_DERR_OFFSETS);
+            return;
+        }
+        if (e > a) atomicOr(start + ((b0 + a) >> 6), 1ULL << (63 - ((b0 + a) & 63)));
+    }
+}
+
+void launch_mark_starts_sets(const uint64_t* offsets, const uint64_t* off0, const uint64_t* n_reads,
+                             const uint64_t* base, uint32_t n_sets, uint64_t max_reads, char* reads,
+                             uint64_t* start_mask, int* err, cudaStream_t st) {
+    if (n_sets == 0) return;
+    count_launch();
+    uint64_t bx = (max_reads + 255) / 256;
+    if (bx < 1) bx = 1;
+    if (bx > 1024) bx = 1024;
+    k_mark_starts_sets<<<dim3((unsigned)bx, n_sets), 256, 0, st>>>(offsets, off0, n_reads, base, reads,
+                                                                   (u64*)start_mask, err);
+}
+
 void launch_encode(const char* reads, uint64_t n_bases, uint64_t* packed, uint64_t* invalid,
                    uint64_t n_packed_words, uint64_t n_mask_words, cudaStream_t st) {
     uint64_t threads = (n_bases + 63) / 64;

@@ -490,6 +490,11 @@ __device__ __forceinline__ void ls_prefetch(K (&pf)[PFN], const K* keys, const u
 // written to keys[sub_off[s] + i] and kcount[sub_off[s] + i], i < kc[s]
 // (in no particular order: stage S6 orders all pairs).  The counts of all
 // runs go to the histogram, their number to n_distinct, the largest to max_count.
+// Packed sets (grp_set != nullptr): group g belongs to set grp_set[g] and the
+// statistics of its sub-segments (g * 256 + digit) go to that set's
+// histogram hist + set * hist_len, n_distinct[set] and max_count[set].  A CTA
+// takes sub-segments in ascending order, so the sets it meets ascend too; it
+// keeps one set's statistics on chip and flushes them when the set changes.
 template <typename K, bool BIG>
 __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(const u64* __restrict__ sub_off,
                                                       const uint32_t* __restrict__ only, uint32_t n_sub, int shift0,
@@ -498,7 +503,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                                                       unsigned long long* ov_stats, uint32_t lo, uint32_t hi,
                                                       u64* __restrict__ hist, uint32_t hist_len,
                                                       uint32_t* max_count, unsigned long long* n_distinct,
-                                                      uint32_t* claim, int* err) {
+                                                      const uint32_t* __restrict__ grp_set, uint32_t* claim,
+                                                      int* err) {
     using Cfg = LocalCfg<K, BIG>;
     constexpr int CAP = Cfg::CAP;
     constexpr int NT = BIG ? 512 : 256;   // threads
@@ -526,16 +532,42 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
     u64 my_distinct = 0;
     uint32_t my_max = 0, my_ones = 0;
     u64 base = 0;
+    uint32_t cur_set = 0xFFFFFFFFu;  // set whose statistics are held on chip (none yet)
+    u64* hcur = hist;
     auto count_run = [&](uint32_t cnt) {
         if (cnt == 1) {
             ++my_ones;
         } else {
             const uint32_t b = cnt < hist_len - 1 ? cnt : hist_len - 1;
             if (b < hs) atomicAdd(&s_hist[b], 1u);
-            else atomicAdd(reinterpret_cast<unsigned long long*>(hist + b), 1ULL);
+            else atomicAdd(reinterpret_cast<unsigned long long*>(hcur + b), 1ULL);
         }
         ++my_distinct;
         my_max = cnt > my_max ? cnt : my_max;
+    };
+    // the held statistics -> set `set` (all threads; leaves them cleared)
+    auto flush_stats = [&](uint32_t set) {
+        if (my_ones) atomicAdd(&s_hist[1], my_ones);  // hist_len >= 2: count 1 has its own bin
+        __syncthreads();
+        u64* h = hist + (u64)set * hist_len;
+        for (uint32_t i = tid; i < hs; i += NT) {
+            const uint32_t v = s_hist[i];
+            if (v) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(h + i), (unsigned long long)v);
+                s_hist[i] = 0;
+            }
+        }
+        const u64 d = warp_incl_sum<u64>(my_distinct);
+        uint32_t mx = my_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t v = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = v > mx ? v : mx;
+        }
+        if (lane == 31 && d) atomicAdd(n_distinct + set, (unsigned long long)d);
+        if (lane == 0 && mx) atomicMax(max_count + set, mx);
+        my_distinct = 0;
+        my_max = my_ones = 0;
+        __syncthreads();
     };
     // one run, from a single lane
     auto emit = [&](const K& key, uint32_t cnt) {
@@ -582,6 +614,14 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
         const u64 n64 = sub_off[s + 1] - base;
         __syncthreads();  // every thread has read s_next; the last sub-segment's shared state is free
         if (tid == 0) s_next = atomicAdd(claim, 1u);
+        {
+            const uint32_t set = grp_set ? grp_set[s >> 8] : 0u;  // CTA-uniform
+            if (set != cur_set) {
+                if (cur_set != 0xFFFFFFFFu) flush_stats(cur_set);
+                cur_set = set;
+                hcur = hist + (u64)set * hist_len;
+            }
+        }
         if (n64 == 0 || n64 > (u64)CAP) {
             if (tid == 0) {
                 kc[s] = 0;
@@ -827,25 +867,14 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
         for (int j = 0; j < BPT; ++j) s_cnt1[tid * BPT + j] = 0;
         si = nxt;
     }
-    if (my_ones) atomicAdd(&s_hist[1], my_ones);  // hist_len >= 2: count 1 has its own bin
-    __syncthreads();
-    for (uint32_t i = tid; i < hs; i += NT)
-        if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(hist + i), (unsigned long long)s_hist[i]);
-    // per-CTA totals
-    my_distinct = warp_incl_sum<u64>(my_distinct);
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint32_t v = __shfl_xor_sync(0xffffffffu, my_max, o);
-        my_max = v > my_max ? v : my_max;
-    }
-    if (lane == 31 && my_distinct) atomicAdd(n_distinct, (unsigned long long)my_distinct);
-    if (lane == 0 && my_max) atomicMax(max_count, my_max);
+    if (cur_set != 0xFFFFFFFFu) flush_stats(cur_set);
 }
 
 void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, bool big, int shift0,
                        int key_words, void* keys, uint32_t* kcount, uint32_t* kc, uint32_t* ov_list,
                        uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
-                       uint32_t* max_count, uint64_t* n_distinct, uint32_t* claim, int* err, int num_sms,
-                       cudaStream_t st) {
+                       uint32_t* max_count, uint64_t* n_distinct, const uint32_t* grp_set, uint32_t* claim,
+                       int* err, int num_sms, cudaStream_t st) {
     if (n_sub == 0) return;
     count_launch();
     const size_t dyn = local_smem_bytes(key_words, big);
@@ -860,7 +889,7 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
         if (want < g) g = want;
         kern<<<(unsigned)g, nt, dyn, st>>>((const u64*)sub_off, only, n_sub, shift0, kp, kcount, kc, ov_list,
                                               (unsigned long long*)ov_stats, lo, hi, (u64*)hist, hist_len,
-                                              max_count, (unsigned long long*)n_distinct, claim, err);
+                                              max_count, (unsigned long long*)n_distinct, grp_set, claim, err);
     };
     if (key_words == 1) {
         if (big) go(k_local_sort<u64, true>, (u64*)keys);

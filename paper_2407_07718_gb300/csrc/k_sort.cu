@@ -213,6 +213,69 @@ void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hi
         k_digit_hist<key128><<<g, 256, 0, st>>>((const key128*)keys, n, (u64*)hist, n_pass);
 }
 
+// Digit histograms of C consecutive segments of plain keys: hist[c][p][256]
+// for keys [key_base[c], key_base[c + 1]).  Block b takes keys [b * chunk,
+// (b + 1) * chunk) and counts the segments that range meets one after the
+// other, flushing each segment's counts before starting the next.
+template <typename K>
+__global__ void __launch_bounds__(256) k_digit_hist_seg(const K* __restrict__ keys, const u64* __restrict__ key_base,
+                                                        uint32_t C, u64 n, u64 chunk, u64* __restrict__ hist,
+                                                        int n_pass) {
+    __shared__ uint32_t s_hist[MAX_PASS * RADIX];
+    const u64 r0 = (u64)blockIdx.x * chunk;
+    const u64 r1 = r0 + chunk < n ? r0 + chunk : n;
+    if (r0 >= r1) return;
+    uint32_t c = 0, hi = C;  // key_base[c] <= r0 < key_base[hi]
+    while (hi - c > 1) {
+        const uint32_t mid = (c + hi) >> 1;
+        if (key_base[mid] <= r0) c = mid;
+        else hi = mid;
+    }
+    for (; c < C && key_base[c] < r1; ++c) {
+        const u64 a = key_base[c] > r0 ? key_base[c] : r0;
+        const u64 b = key_base[c + 1] < r1 ? key_base[c + 1] : r1;
+        if (a >= b) continue;  // empty segment (uniform)
+        for (int i = threadIdx.x; i < n_pass * RADIX; i += 256) s_hist[i] = 0;
+        __syncthreads();
+        for (u64 i = a + threadIdx.x; i < b; i += 256) {
+            const K key = keys[i];
+            for (int p = 0; p < n_pass; ++p) atomicAdd(&s_hist[p * RADIX + key_digit(key, 8 * p, 0xFF)], 1u);
+        }
+        __syncthreads();
+        u64* h = hist + (u64)c * n_pass * RADIX;
+        for (int i = threadIdx.x; i < n_pass * RADIX; i += 256)
+            if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(h + i), (unsigned long long)s_hist[i]);
+        __syncthreads();
+    }
+}
+
+void launch_digit_hist_seg(const void* keys, int key_words, const uint64_t* key_base, uint32_t C, uint64_t n,
+                           uint64_t* hist, int n_pass, cudaStream_t st) {
+    if (n == 0 || C == 0) return;
+    count_launch();
+    const u64 chunk = 32768;
+    const unsigned g = (unsigned)((n + chunk - 1) / chunk);
+    if (key_words == 1)
+        k_digit_hist_seg<u64><<<g, 256, 0, st>>>((const u64*)keys, (const u64*)key_base, C, n, chunk, (u64*)hist,
+                                                 n_pass);
+    else
+        k_digit_hist_seg<key128><<<g, 256, 0, st>>>((const key128*)keys, (const u64*)key_base, C, n, chunk,
+                                                    (u64*)hist, n_pass);
+}
+
+// dst[i] = src[idx[i]], i < n
+__global__ void k_gather_u64(const u64* __restrict__ src, const u64* __restrict__ idx, uint32_t n,
+                             u64* __restrict__ dst) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
+}
+
+void launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint32_t n, uint64_t* dst, cudaStream_t st) {
+    if (n == 0) return;
+    count_launch();
+    const unsigned g = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    k_gather_u64<<<g, 256, 0, st>>>((const u64*)src, (const u64*)idx, n, (u64*)dst);
+}
+
 // doff[(p * C + c) * 256 + d] = key_base[c] + sum over d' < d of hist[(c * P + p) * 256 + d']
 __global__ void __launch_bounds__(256) k_digit_offsets_seg(const u64* __restrict__ hist, const u64* __restrict__ key_base,
                                                            u64* __restrict__ doff, int n_pass, uint32_t C) {
@@ -253,6 +316,30 @@ uint64_t onesweep_tile_keys(int key_words) {
     return 256ull * (key_words == 1 ? PassCfg<u64>::ITEMS : PassCfg<key128>::ITEMS);
 }
 
+// Segment c and its tile j of global tile g, and the first status tile of
+// the segment.  Interleaved (tile_start == nullptr): segment g % C, tile
+// g / C, status tiles [c * tmax, (c + 1) * tmax).  Listed: segment c owns
+// the consecutive global tiles [tile_start[c], tile_start[c + 1]) (C + 1
+// entries, empty segments repeat an entry) and their status tiles.
+__device__ __forceinline__ void seg_tile(uint32_t g, uint32_t C, uint32_t tmax, const uint32_t* tile_start,
+                                         uint32_t& c, uint32_t& j, u64& st0) {
+    if (tile_start) {
+        uint32_t lo = 0, hi = C;  // tile_start[lo] <= g < tile_start[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tile_start[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        c = lo;
+        j = g - tile_start[lo];
+        st0 = tile_start[lo];
+    } else {
+        c = g % C;
+        j = g / C;
+        st0 = (u64)c * tmax;
+    }
+}
+
 __device__ __forceinline__ u64 load_stream(const u64* p) { return __ldcs(reinterpret_cast<const unsigned long long*>(p)); }
 __device__ __forceinline__ key128 load_stream(const key128* p) {
     ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(p));
@@ -267,8 +354,8 @@ template <typename K, bool HAS_VAL>
 __global__ void __launch_bounds__(256, HAS_VAL ? 3 : 4)
     k_onesweep_seg(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
                    uint32_t* __restrict__ vout, const u64* __restrict__ key_base, uint32_t C, uint32_t tmax,
-                   int shift, const u64* __restrict__ doff, u64* status, uint32_t* tile_ctr, uint32_t epoch,
-                   int* err) {
+                   const uint32_t* __restrict__ tile_start, int shift, const u64* __restrict__ doff, u64* status,
+                   uint32_t* tile_ctr, uint32_t epoch, int* err) {
     constexpr int ITEMS = PassCfg<K>::ITEMS;
     constexpr int TILE = 256 * ITEMS;
     constexpr int WARPS = 8;
@@ -286,7 +373,9 @@ __global__ void __launch_bounds__(256, HAS_VAL ? 3 : 4)
     for (int i = threadIdx.x; i < WARPS * RADIX; i += 256) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t g = s_tile;
-    const uint32_t c = g % C, tile = g / C;
+    uint32_t c, tile;
+    u64 st0;
+    seg_tile(g, C, tmax, tile_start, c, tile, st0);
     const u64 sb = key_base[c], sn = key_base[c + 1] - sb;
     if ((u64)tile * TILE >= sn) return;  // this segment has fewer tiles (uniform exit)
     const u64 base = sb + (u64)tile * TILE;
@@ -340,7 +429,7 @@ __global__ void __launch_bounds__(256, HAS_VAL ? 3 : 4)
     // have left the registers).  Status words are laid out [segment][tile]
     // [digit]: a tile publishes its 256 words into 2 KB of its own, so tiles
     // never contend for the same L2 sectors.
-    u64* seg_status = status + (u64)c * tmax * RADIX;
+    u64* seg_status = status + st0 * RADIX;
     u64* my = seg_status + (u64)tile * RADIX + d;
     if (tile == 0) st_relaxed(my, lb_word(LB_PREFIX, epoch, cnt));
     else st_relaxed(my, lb_word(LB_AGG, epoch, cnt));
@@ -383,17 +472,17 @@ __global__ void __launch_bounds__(256, HAS_VAL ? 3 : 4)
 
 template <typename K, bool HV>
 static void launch_pass_t(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, const uint64_t* key_base,
-                          uint32_t C, uint32_t tmax, int shift, const uint64_t* doff, uint64_t* status,
-                          uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st) {
+                          uint32_t C, uint32_t tmax, const uint32_t* tile_start, int shift, const uint64_t* doff,
+                          uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err, cudaStream_t st) {
     constexpr int TILE = 256 * PassCfg<K>::ITEMS;
     size_t smem = (size_t)TILE * sizeof(K) + (HV ? (size_t)TILE * sizeof(uint32_t) : 0);
     auto fn = k_onesweep_seg<K, HV>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     count_launch();
-    fn<<<(unsigned)((uint64_t)C * tmax), 256, smem, st>>>((const K*)kin, (K*)kout, vin, vout, (const u64*)key_base,
-                                                          C, tmax, shift, (const u64*)doff, (u64*)status, tile_ctr,
-                                                          epoch, err);
+    const uint64_t blocks = tile_start ? (uint64_t)tmax : (uint64_t)C * tmax;
+    fn<<<(unsigned)blocks, 256, smem, st>>>((const K*)kin, (K*)kout, vin, vout, (const u64*)key_base, C, tmax,
+                                            tile_start, shift, (const u64*)doff, (u64*)status, tile_ctr, epoch, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,8 +527,8 @@ static_assert(TmaCfg<key128>::NT * TmaCfg<key128>::ITEMS == 256 * PassCfg<key128
 template <typename K>
 __global__ void __launch_bounds__(TmaCfg<K>::NT, HSK_TMA_CTAS)
     k_onesweep_tma(const K* __restrict__ kin, K* __restrict__ kout, const u64* __restrict__ key_base, uint32_t C,
-                   uint32_t tmax, int shift, const u64* __restrict__ doff, u64* status, uint32_t* tile_ctr,
-                   uint32_t epoch, int* err) {
+                   uint32_t tmax, const uint32_t* __restrict__ tile_start, int shift, const u64* __restrict__ doff,
+                   u64* status, uint32_t* tile_ctr, uint32_t epoch, int* err) {
     constexpr int NT = TmaCfg<K>::NT;
     constexpr int ITEMS = TmaCfg<K>::ITEMS;
     constexpr int TILE = NT * ITEMS;
@@ -453,11 +542,13 @@ __global__ void __launch_bounds__(TmaCfg<K>::NT, HSK_TMA_CTAS)
     __shared__ __align__(8) u64 s_bar[2];
     __shared__ uint32_t s_next;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t total = C * tmax;
+    const uint32_t total = tile_start ? tmax : C * tmax;
 
-    // geometry of global tile g: segment g % C, tile g / C of that segment
+    // geometry of global tile g (seg_tile)
     auto geom = [&](uint32_t g, u64& sb, u64& seg_end, u64& base, uint32_t& n_t) -> bool {
-        const uint32_t c = g % C, j = g / C;
+        uint32_t c, j;
+        u64 st0;
+        seg_tile(g, C, tmax, tile_start, c, j, st0);
         sb = key_base[c];
         seg_end = key_base[c + 1];
         base = sb + (u64)j * TILE;
@@ -562,8 +653,10 @@ __global__ void __launch_bounds__(TmaCfg<K>::NT, HSK_TMA_CTAS)
                     cnt += cc;
                 }
             }
-            const uint32_t c = g % C, tile = g / C;
-            u64* seg_status = status + (u64)c * tmax * RADIX;
+            uint32_t c, tile;
+            u64 st0;
+            seg_tile(g, C, tmax, tile_start, c, tile, st0);
+            u64* seg_status = status + st0 * RADIX;
             u64* my = seg_status + (u64)tile * RADIX + d;
             if (dig) {
                 if (tile == 0) st_relaxed(my, lb_word(LB_PREFIX, epoch, cnt));
@@ -616,16 +709,16 @@ __global__ void __launch_bounds__(TmaCfg<K>::NT, HSK_TMA_CTAS)
 }
 
 void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
-                         const uint64_t* key_base, uint32_t C, uint32_t tmax, int key_words, int shift,
-                         const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr, uint32_t epoch, int* err,
-                         cudaStream_t st) {
+                         const uint64_t* key_base, uint32_t C, uint32_t tmax, const uint32_t* tile_start,
+                         int key_words, int shift, const uint64_t* doff, uint64_t* status, uint32_t* tile_ctr,
+                         uint32_t epoch, int* err, cudaStream_t st) {
     if (C == 0 || tmax == 0) return;
     bool hv = vin != nullptr;
     if (!hv && key_words == 2) {
         // 128-bit keys alone: the tile-per-CTA pass (the persistent TMA pass
         // below measured slower for them: 1.5 against 2.7 TB/s)
-        launch_pass_t<key128, false>(kin, kout, nullptr, nullptr, key_base, C, tmax, shift, doff, status, tile_ctr,
-                                     epoch, err, st);
+        launch_pass_t<key128, false>(kin, kout, nullptr, nullptr, key_base, C, tmax, tile_start, shift, doff, status,
+                                     tile_ctr, epoch, err, st);
         return;
     }
     if (!hv) {  // persistent, TMA-staged pass
@@ -636,25 +729,30 @@ void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint3
             cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
             if (num_sms <= 0) num_sms = 1;
         }
-        const uint64_t tiles = (uint64_t)C * tmax;
+        const uint64_t tiles = tile_start ? (uint64_t)tmax : (uint64_t)C * tmax;
         const unsigned grid = (unsigned)(tiles < (uint64_t)num_sms * HSK_TMA_CTAS ? tiles : (uint64_t)num_sms * HSK_TMA_CTAS);
         count_launch();
         if (key_words == 1) {
             const size_t smem = 2 * (size_t)tma_buf_bytes<u64>();
             cudaFuncSetAttribute(k_onesweep_tma<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_onesweep_tma<u64><<<grid, TmaCfg<u64>::NT, smem, st>>>((const u64*)kin, (u64*)kout, (const u64*)key_base, C, tmax,
-                                                         shift, (const u64*)doff, (u64*)status, tile_ctr, epoch, err);
+                                                         tile_start, shift, (const u64*)doff, (u64*)status, tile_ctr,
+                                                         epoch, err);
         } else {
             const size_t smem = 2 * (size_t)tma_buf_bytes<key128>();
             cudaFuncSetAttribute(k_onesweep_tma<key128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_onesweep_tma<key128><<<grid, TmaCfg<key128>::NT, smem, st>>>((const key128*)kin, (key128*)kout, (const u64*)key_base,
-                                                            C, tmax, shift, (const u64*)doff, (u64*)status, tile_ctr,
-                                                            epoch, err);
+                                                            C, tmax, tile_start, shift, (const u64*)doff, (u64*)status,
+                                                            tile_ctr, epoch, err);
         }
         return;
     }
-    if (key_words == 1) launch_pass_t<u64, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
-    else launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, shift, doff, status, tile_ctr, epoch, err, st);
+    if (key_words == 1)
+        launch_pass_t<u64, true>(kin, kout, vin, vout, key_base, C, tmax, tile_start, shift, doff, status, tile_ctr,
+                                 epoch, err, st);
+    else
+        launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, tile_start, shift, doff, status,
+                                    tile_ctr, epoch, err, st);
 }
 
 // ---------------------------------------------------------------------------

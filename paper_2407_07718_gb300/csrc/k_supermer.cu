@@ -168,6 +168,18 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
 
     for (u64 t = P.tile_begin + (u64)blockIdx.x * SM_WARPS + warp; t < n_tiles; t += (u64)gridDim.x * SM_WARPS) {
         const u64 p0 = t * SM_TW;
+        // buckets of the tile's set (packed sets: the set holding tile t)
+        uint32_t bbase = 0, bmask = B - 1u;
+        if (P.n_sets) {
+            uint32_t lo = 0, hi = P.n_sets;  // set_tile0[lo] <= t < set_tile0[hi]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((u64)P.set_tile0[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            bbase = P.set_bucket[lo];
+            bmask = P.set_bmask[lo];
+        }
         // ---- stage packed bases and masks (128-bit loads; p0 is 1024-aligned)
         {
             const u64 pw0 = p0 >> 5, mw0 = p0 >> 6;
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
             const u64 p = p0 + lp;
             int valid = (p + k <= P.n_bases) && ((wval[lp >> 6] >> (63 - (lp & 63))) & 1);
             const uint32_t mh = window_min<NREG>(X, w, lane);
-            const uint32_t b = mh & (B - 1u);
+            const uint32_t b = bbase + (mh & bmask);
 
             if (MODE == SM_DUMP) {
                 if (p < P.n_bases) {
