@@ -192,14 +192,28 @@ def run_cpu_oracle(rs, target_windows: int, steps: int = 1):
 # batched and served forms against the plain per-job path
 # ---------------------------------------------------------------------------
 
+_PINNED = []
+
+
 def _pinned(rs):
-    """The read set's arrays copied into page-locked host memory."""
-    import torch
-    r = torch.empty(rs.n_bases, dtype=torch.uint8, pin_memory=True)
-    r.numpy()[:] = rs.reads
-    o = torch.empty(rs.offsets.size, dtype=torch.int64, pin_memory=True)
-    o.numpy()[:] = rs.offsets.view(np.int64)
-    return (r.numpy(), o.numpy().view(np.uint64), rs.k, rs.m, rs.lo, rs.hi)
+    """The read set's reads and offsets copied into one page-locked host
+    buffer of exactly their size (hsk_host_pin; see _unpin_all)."""
+    import paper_2407_07718_gb300 as hsk
+    ob = rs.offsets.size * 8
+    rb = (rs.n_bases + 63) // 64 * 64
+    buf = hsk.pinned_empty(ob + rb)
+    offs = buf[:ob].view(np.uint64)
+    offs[:] = rs.offsets
+    reads = buf[ob:ob + rs.n_bases]
+    reads[:] = rs.reads
+    _PINNED.append(buf)
+    return (reads, offs, rs.k, rs.m, rs.lo, rs.hi)
+
+
+def _unpin_all():
+    import paper_2407_07718_gb300 as hsk
+    while _PINNED:
+        hsk.host_unpin(_PINNED.pop())
 
 
 def _generate(fn, params):
@@ -233,7 +247,7 @@ def _plain_pass(ctx, jobs):
     return times, res
 
 
-def bench_batched(hsk, device: int, n_sets: int, scale: float) -> dict:
+def bench_batched(hsk, device: int, n_sets: int, scale: float, tune_trials: int = 12) -> dict:
     import datagen
     params = datagen.batched_set_params(n_sets=n_sets, scale=scale)
     t0 = time.perf_counter()
@@ -244,12 +258,22 @@ def bench_batched(hsk, device: int, n_sets: int, scale: float) -> dict:
         big = max(range(len(jobs)), key=lambda i: jobs[i][0].size)
         ctx.count(*jobs[big], copy=False)          # warm: the arena grows to the largest set
         plain_t, plain_r = _plain_pass(ctx, jobs)
+        # the autotuner picks the forms' parameters on a sample of the sets
+        # (every fourth one), timing candidates through hsk_count_batch
+        t0 = time.perf_counter()
+        tuned = ctx.autotune(jobs[::4], max_trials=tune_trials) if tune_trials else ctx.tune_current()
+        tune_s = time.perf_counter() - t0
         ctx.count_batch(jobs, copy=False)           # warm: every slot grows its arena
+        p0 = ctx.pack_stats()
         t0 = time.perf_counter()
         batch_r = ctx.count_batch(jobs, copy=False)
         batch_s = time.perf_counter() - t0
+        p1 = ctx.pack_stats()
+        packs = {key: p1[key] - p0[key] for key in p1}
     for a, b in zip(plain_r, batch_r):
         assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct, b.extra["n_pairs"])
+    del jobs
+    _unpin_all()
     n = sum(r.n_windows for r in plain_r)
     plain_s = sum(plain_t)
     return {"workload": f"{n_sets} sets, genome log-uniform [0.1, 20] Mbp x {scale:g}, coverage U[10, 40]x, "
@@ -258,59 +282,110 @@ def bench_batched(hsk, device: int, n_sets: int, scale: float) -> dict:
             "plain": {"value": n / plain_s, "makespan_s": plain_s,
                       "job_p50_ms": _pct(plain_t, 50) * 1e3, "job_p99_ms": _pct(plain_t, 99) * 1e3},
             "batched": {"value": n / batch_s, "makespan_s": batch_s},
-            "speedup": plain_s / batch_s, "unit": UNIT,
+            "speedup": plain_s / batch_s, "unit": UNIT, "pack_stats": packs,
+            "autotune": dict(tuned, tune_s=tune_s, sample="every 4th set"),
             "note": "makespans include host-to-device copies from pinned memory and result copies back"}
 
 
-def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget: int) -> dict:
+def _mem_available() -> int:
+    """Host memory the kernel reports as available (bytes), or 0 if unknown."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget: int,
+                 tune_trials: int = 8) -> dict:
+    """The Poisson request stream, its inputs held in pinned host memory.
+
+    The stream's inputs are generated up front.  When they would take more
+    than 45 % of the host's available memory (results, the library's host
+    pool and the tuner's trial batches need room beside them), the stream is
+    run as consecutive blocks, each generated before it starts, at the same
+    offered rate, and the latencies of all blocks are pooled; the line says how
+    many blocks were used."""
     import datagen
     params = datagen.served_request_params(n=n_req, scale=scale)
-    t0 = time.perf_counter()
-    jobs = _generate(datagen.served_request, params)
-    gen_s = time.perf_counter() - t0
+    need = sum(int(g * c * 1.06) + 4096 for (_, g, c, _, _, _) in params)  # bases + offsets
+    avail = _mem_available()
+    n_blocks = 1
+    if avail and need > 0.45 * avail:
+        n_blocks = int(np.ceil(need / max(0.45 * avail, 4e9)))
+    blocks = [params[i * len(params) // n_blocks:(i + 1) * len(params) // n_blocks] for i in range(n_blocks)]
+    gen_s = plain_s = sat_s = open_s = tune_s = 0.0
+    n = 0
+    lat, plain_lat = [], []
+    rate = None
+    tuned = None
+    packs = {"passes": 0, "sets": 0, "alone": 0}
     with hsk.Context(device=device, hbm_budget=budget) as ctx:
-        for kk in sorted({j[2] for j in jobs}):     # warm each key width on the largest request
-            big = max((i for i in range(len(jobs)) if jobs[i][2] == kk), key=lambda i: jobs[i][0].size)
-            ctx.count(*jobs[big], copy=False)
-        plain_t, plain_r = _plain_pass(ctx, jobs)
-        n = sum(r.n_windows for r in plain_r)
-
-        def closed_batch():
+        for bi, bparams in enumerate(blocks):
             t0 = time.perf_counter()
-            ts = [ctx.submit(*j) for j in jobs]
-            for t in ts:
-                ctx.wait(t, copy=False)
-            dt = time.perf_counter() - t0
-            for t in ts:
-                ctx.release(t)
-            return dt
+            jobs = _generate(datagen.served_request, bparams)
+            gen_s += time.perf_counter() - t0
+            if bi == 0:
+                for kk in sorted({j[2] for j in jobs}):     # warm each key width on the largest request
+                    big = max((i for i in range(len(jobs)) if jobs[i][2] == kk), key=lambda i: jobs[i][0].size)
+                    ctx.count(*jobs[big], copy=False)
+            plain_t, plain_r = _plain_pass(ctx, jobs)
+            n_b = sum(r.n_windows for r in plain_r)
+            n += n_b
+            plain_s += sum(plain_t)
+            if bi == 0:
+                t0 = time.perf_counter()
+                tuned = ctx.autotune(jobs[::20], max_trials=tune_trials) if tune_trials else ctx.tune_current()
+                tune_s = time.perf_counter() - t0
 
-        closed_batch()                              # warm the slots
-        sat_s = closed_batch()
-        rate = load * len(jobs) / sat_s             # requests per second offered
-        gaps = np.random.default_rng(5).exponential(1.0 / rate, len(jobs))
-        arrivals = np.cumsum(gaps) - gaps[0]
-        tickets = []
-        t0 = time.perf_counter()
-        for i, j in enumerate(jobs):
-            while True:
-                d = arrivals[i] - (time.perf_counter() - t0)
-                if d <= 0:
-                    break
-                time.sleep(min(d, 0.002))
-            tickets.append(ctx.submit(*j))
-        res = [ctx.wait(t, copy=False) for t in tickets]
-        open_s = time.perf_counter() - t0
-        lat = [sum(ctx.times(t)) for t in tickets]
-        for t in tickets:
-            ctx.release(t)
-    for a, b in zip(plain_r, res):
-        assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct, b.extra["n_pairs"])
-    plain_s = sum(plain_t)
-    plain_lat = _fifo_latency(arrivals, plain_t)
+            def closed_batch():
+                # results are released as they are read: a completed request's
+                # host arrays go back to the library's pool for later requests
+                t0 = time.perf_counter()
+                ts = [ctx.submit(*j) for j in jobs]
+                for t in ts:
+                    ctx.wait(t, copy=False)
+                    ctx.release(t)
+                return time.perf_counter() - t0
+
+            closed_batch()                              # warm the slots
+            p0 = ctx.pack_stats()
+            sat_b = closed_batch()
+            sat_s += sat_b
+            if rate is None:
+                rate = load * len(jobs) / sat_b         # requests per second offered (first block)
+            gaps = np.random.default_rng(5 + bi).exponential(1.0 / rate, len(jobs))
+            arrivals = np.cumsum(gaps) - gaps[0]
+            tickets = []
+            t0 = time.perf_counter()
+            for i, j in enumerate(jobs):
+                while True:
+                    d = arrivals[i] - (time.perf_counter() - t0)
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 0.002))
+                tickets.append(ctx.submit(*j))
+            res = []
+            for t in tickets:
+                res.append(ctx.wait(t, copy=False))
+                lat.append(sum(ctx.times(t)))
+                ctx.release(t)
+            open_s += time.perf_counter() - t0
+            p1 = ctx.pack_stats()
+            for key in packs:
+                packs[key] += p1[key] - p0[key]
+            for a, b in zip(plain_r, res):
+                assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct,
+                                                                          b.extra["n_pairs"])
+            plain_lat += _fifo_latency(arrivals, plain_t)
+            del jobs, plain_r, res
+            _unpin_all()
     return {"workload": f"{n_req} Poisson requests, genome log-normal (median 2 Mbp, sigma_ln 1, [0.05, 50] Mbp) "
                         f"x {scale:g}, coverage U[10, 30]x, 150 bp or 10 kb reads, k in {{21, 31, 55}}, filter [2,1000]",
             "n_requests": n_req, "n_windows": n, "generate_s": gen_s, "hbm_budget": budget,
+            "blocks": n_blocks, "host_input_bytes": need,
             "offered_rate_per_s": rate, "load": load,
             "served": {"value_saturated": n / sat_s, "makespan_saturated_s": sat_s,
                        "value": n / open_s, "p50_ms": _pct(lat, 50) * 1e3, "p99_ms": _pct(lat, 99) * 1e3,
@@ -319,7 +394,8 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
                       "p50_ms": _pct(plain_lat, 50) * 1e3, "p99_ms": _pct(plain_lat, 99) * 1e3,
                       "p999_ms": _pct(plain_lat, 99.9) * 1e3,
                       "latency_model": "measured per-job times on one FIFO server at the same arrival times"},
-            "speedup_saturated": plain_s / sat_s, "unit": UNIT,
+            "speedup_saturated": plain_s / sat_s, "unit": UNIT, "pack_stats": packs,
+            "autotune": dict(tuned, tune_s=tune_s, sample="every 20th request of the first block"),
             "note": "latency = submit to completion; copies from pinned host memory inside every job"}
 
 
@@ -449,7 +525,8 @@ def main():
     ap.add_argument("--second-steps", type=int, default=5)
     ap.add_argument("--batched-sets", type=int, default=256)
     ap.add_argument("--batched-scale", type=float, default=1.0)
-    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--tune-trials", type=int, default=10, help="autotuner trials before the forms (0 = none)")
     ap.add_argument("--served-scale", type=float, default=1.0)
     ap.add_argument("--served-load", type=float, default=0.7)
     ap.add_argument("--served-budget", type=float, default=120e9)
@@ -619,15 +696,19 @@ def main():
     ctx.close()
     del d_reads, d_offs
     forms = {}
+    def leg(name, fn):  # each extra leg is also logged to stderr as soon as it ends
+        forms[name] = fn()
+        print(json.dumps({name: forms[name]}), file=sys.stderr, flush=True)
+
     if rank == 0 and world == 1 and args.second_workload not in ("none", args.workload):
         torch.cuda.empty_cache()
-        forms[args.second_workload] = bench_second_workload(hsk, local, args.second_workload, args.second_steps,
-                                                            args.warmup)
+        leg(args.second_workload, lambda: bench_second_workload(hsk, local, args.second_workload, args.second_steps,
+                                                                args.warmup))
     if rank == 0 and world == 1 and not args.no_forms:
         torch.cuda.empty_cache()
-        forms["batched"] = bench_batched(hsk, local, args.batched_sets, args.batched_scale)
-        forms["served"] = bench_served(hsk, local, args.served_requests, args.served_scale, args.served_load,
-                                       int(args.served_budget))
+        leg("batched", lambda: bench_batched(hsk, local, args.batched_sets, args.batched_scale, args.tune_trials))
+        leg("served", lambda: bench_served(hsk, local, args.served_requests, args.served_scale, args.served_load,
+                                           int(args.served_budget), args.tune_trials))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

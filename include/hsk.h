@@ -59,11 +59,15 @@ typedef struct {
     uint32_t radix_bits;   /* LSD digit width, 8 (default) */
     uint32_t max_chunk_kmers; /* 0 = as many as the budget allows; else cap per sort chunk */
     uint64_t seed;         /* XOR-ed into each canonical m-mer before hashing */
-    int autotune;          /* 1 = pick bucket count and chunking per job */
+    int autotune;          /* 1 = hsk_count_batch applies the parameters that
+                              hsk_autotune recorded for its class of job mix (if
+                              any); 0 = built-in or last applied parameters */
     int local_sort;        /* 1 (default) = sort and count sub-segments that fit in
                               shared memory on chip, the rest with global radix
                               passes; 0 = global radix passes only.  The result is
                               the same either way. */
+    const char* tune_cache; /* file of tuned parameters: read at hsk_create,
+                               appended to by hsk_autotune; NULL = none */
 } hsk_config;
 
 /* A counting result.  All arrays are owned by the context and stay valid until
@@ -97,7 +101,7 @@ typedef struct {
 } hsk_job;
 
 /* Defaults: device 0, budget 0 (90 % of free), hist_len 65536, buckets auto,
- * 8-bit digits, seed 0x9E3779B97F4A7C15, autotune on. */
+ * 8-bit digits, seed 0x9E3779B97F4A7C15, autotune on, no tuning cache. */
 int hsk_config_default(hsk_config* cfg);
 
 /* Create a context on cfg->device (cfg = NULL: defaults).  *out receives the
@@ -139,12 +143,63 @@ int hsk_count_device(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offset
 int hsk_result_copy(hsk_ctx* ctx, const hsk_result* res, uint64_t* kmers_dst, uint32_t* counts_dst,
                     uint64_t* hist_dst, int dst_on_device, void* stream);
 
-/* Batched form: count n_jobs independent host-resident read sets.  Small
- * jobs are packed together and counted by shared launches captured in a CUDA
- * graph; each outs[i] is bit-identical to what hsk_count() returns for jobs[i]
- * alone.  Result arrays are host memory owned by the context, valid until the
- * next counting call.  Errors as hsk_count; on error no result is valid. */
+/* Batched form: count n_jobs independent host-resident read sets.  The jobs
+ * are queued, largest first, on the context's serving slots (child contexts
+ * with their own streams and device arenas, running side by side).  A job of
+ * at most the pack limit of bases (default 2^28) is counted together with
+ * other queued small jobs of the same k, m, lo and hi by one pass of the
+ * pipeline: their bases share one device buffer, each job owns a range of
+ * minimizer buckets, and every launch serves all of them (Sec. 3.4's
+ * independent tasks on shared workers).  Larger jobs run alone.  Each outs[i]
+ * is bit-identical to what hsk_count() returns for jobs[i] alone, except
+ * n_supermers and device_ms, which describe the pass that counted it (a
+ * packed pass forms supermers with its own bucket count and times all its
+ * jobs together).  Result arrays are host memory owned by the context, valid
+ * until the next counting call.  With hsk_config.autotune set, the call first
+ * applies the parameters hsk_autotune recorded for this class of job mix.
+ * Errors as hsk_count; every job is attempted, and the first failing job's
+ * code is returned with its index in hsk_last_error; on error no result is
+ * valid. */
 int hsk_count_batch(hsk_ctx* ctx, const hsk_job* jobs, uint32_t n_jobs, hsk_result* outs);
+
+/* Page-lock (pin) an existing host buffer of `bytes` bytes so that copies
+ * between it and the device run at link speed (the inputs of hsk_count and of
+ * the batched and served forms); hsk_host_unpin(p) undoes it.  Pinning holds
+ * the pages in RAM until unpinned; the buffer must stay allocated meanwhile.
+ * HSK_ECUDA if the runtime refuses (already pinned, out of lockable memory). */
+int hsk_host_pin(void* p, uint64_t bytes);
+int hsk_host_unpin(void* p);
+
+/* Parameters of the batched and served forms chosen by hsk_autotune. */
+typedef struct {
+    uint32_t group_div;          /* keys of a bucket group = 256 x on-chip sub-segment capacity / group_div */
+    uint32_t plain_bucket_shift; /* large jobs run alone use (4096, or 8192 for k > 32) >> shift buckets */
+    uint64_t pack_bases;         /* bases of one packed pass at most */
+    uint64_t pack_small;         /* jobs of more bases run alone */
+    int slots;                   /* serving slots (streams with their own arenas) */
+    int trials;                  /* timed runs made */
+    double first_s;              /* batch time of the sample with the parameters in force before */
+    double best_s;               /* batch time of the sample with the chosen parameters */
+} hsk_tune_result;
+
+/* Autotuner: runs `jobs` (a sample of the mix to be counted) through
+ * hsk_count_batch under candidate parameters -- slots, pack size, the small-job
+ * limit, the bucket-group size, the bucket count of large jobs -- one
+ * parameter at a time, timing each candidate after a warm-up run of it, at
+ * most max_trials timed runs.  The fastest parameters are applied to the
+ * context and recorded for the jobs' class (key width and binary order of
+ * magnitude of the mean job size), and appended to hsk_config.tune_cache when
+ * set.  *out (may be NULL) receives them.  Errors as hsk_count_batch. */
+int hsk_autotune(hsk_ctx* ctx, const hsk_job* jobs, uint32_t n_jobs, int max_trials, hsk_tune_result* out);
+
+/* The parameters in force on the context (the defaults until hsk_autotune or
+ * a recorded entry changed them); trials, first_s and best_s are 0. */
+int hsk_tune_current(hsk_ctx* ctx, hsk_tune_result* out);
+
+/* Put parameters in force by hand (between calls; trials, first_s and best_s
+ * are ignored).  HSK_EINVAL for values outside group_div 1..64,
+ * plain_bucket_shift 0..4, pack_bases >= 2^20, slots 1..32. */
+int hsk_tune_set(hsk_ctx* ctx, const hsk_tune_result* params);
 
 /* Served form (continuous batching).  hsk_submit queues a job and returns a
  * ticket at once; a worker thread admits queued jobs while the device memory

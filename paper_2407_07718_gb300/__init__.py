@@ -41,7 +41,13 @@ class _Config(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_uint64), ("hist_len", C.c_uint32),
                 ("n_buckets", C.c_uint32), ("radix_bits", C.c_uint32),
                 ("max_chunk_kmers", C.c_uint32), ("seed", C.c_uint64), ("autotune", C.c_int),
-                ("local_sort", C.c_int)]
+                ("local_sort", C.c_int), ("tune_cache", C.c_char_p)]
+
+
+class _TuneResult(C.Structure):
+    _fields_ = [("group_div", C.c_uint32), ("plain_bucket_shift", C.c_uint32), ("pack_bases", C.c_uint64),
+                ("pack_small", C.c_uint64), ("slots", C.c_int), ("trials", C.c_int), ("first_s", C.c_double),
+                ("best_s", C.c_double)]
 
 
 class _Result(C.Structure):
@@ -78,6 +84,11 @@ def load():
             "hsk_count_device": ([P, P, P, u64, u64, i32, i32, u32, u32, P, C.POINTER(_Result)], i32),
             "hsk_result_copy": ([P, C.POINTER(_Result), P, P, P, i32, P], i32),
             "hsk_count_batch": ([P, C.POINTER(_Job), u32, C.POINTER(_Result)], i32),
+            "hsk_autotune": ([P, C.POINTER(_Job), u32, i32, C.POINTER(_TuneResult)], i32),
+            "hsk_tune_current": ([P, C.POINTER(_TuneResult)], i32),
+            "hsk_host_pin": ([P, u64], i32),
+            "hsk_host_unpin": ([P], i32),
+            "hsk_tune_set": ([P, C.POINTER(_TuneResult)], i32),
             "hsk_submit": ([P, C.POINTER(_Job), C.POINTER(u64)], i32),
             "hsk_poll": ([P, u64, C.POINTER(i32)], i32),
             "hsk_wait": ([P, u64, C.POINTER(_Result)], i32),
@@ -138,6 +149,25 @@ def _stream_ptr(stream):
 NOALLOC_MAX_KEYS = {1: 1 << 20, 2: 1 << 19}
 
 
+def pinned_empty(nbytes: int) -> np.ndarray:
+    """A page-aligned host byte buffer of whole pages, pinned with
+    hsk_host_pin (exact size, no rounding).  Call host_unpin(buf) before the
+    buffer is dropped."""
+    import mmap
+    size = max(mmap.PAGESIZE, (int(nbytes) + mmap.PAGESIZE - 1) // mmap.PAGESIZE * mmap.PAGESIZE)
+    buf = np.frombuffer(mmap.mmap(-1, size), dtype=np.uint8)
+    rc = load().hsk_host_pin(C.c_void_p(buf.ctypes.data), size)
+    if rc != HSK_OK:
+        raise HskError(rc, f"hsk_host_pin of {size} bytes failed")
+    return buf
+
+
+def host_unpin(buf: np.ndarray):
+    rc = load().hsk_host_unpin(C.c_void_p(buf.ctypes.data))
+    if rc != HSK_OK:
+        raise HskError(rc, "hsk_host_unpin failed")
+
+
 def sort_keys_noalloc(keys_t, n: int, key_words: int, key_bits: int, stream=None) -> int:
     """Sort n keys of a device tensor in place without any device allocation
     (for callers that cannot allocate; see hsk_sort_keys_noalloc in
@@ -189,13 +219,14 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, hist_len: int = 65536, n_buckets: int = 0,
                  max_chunk_kmers: int = 0, seed: int = DEFAULT_SEED, autotune: bool = True,
-                 local_sort: bool = True):
+                 local_sort: bool = True, tune_cache: str | None = None):
         self.lib = load()
         cfg = _Config()
         self.lib.hsk_config_default(C.byref(cfg))
         cfg.device, cfg.hbm_budget, cfg.hist_len = device, hbm_budget, hist_len
         cfg.n_buckets, cfg.max_chunk_kmers, cfg.seed, cfg.autotune = n_buckets, max_chunk_kmers, seed, int(autotune)
         cfg.local_sort = int(local_sort)
+        cfg.tune_cache = tune_cache.encode() if tune_cache else None
         h = C.c_void_p()
         rc = self.lib.hsk_create(C.byref(h), C.byref(cfg))
         if rc != HSK_OK:
@@ -260,17 +291,42 @@ class Context:
                            int(r.n_chunks), int(r.n_supermers), float(r.device_ms))
 
     # ---- batched form ---------------------------------------------------------
-    def count_batch(self, jobs, copy: bool = True) -> list[CountResult]:
-        """jobs: sequence of (reads, offsets, k, m, lo, hi) host arrays."""
+    @staticmethod
+    def _jobs(jobs):
         keep, arr = [], (_Job * max(len(jobs), 1))()
         for i, (reads, offsets, k, m, lo, hi) in enumerate(jobs):
             reads, offsets = _u8(reads), _u64(offsets)
             keep.append((reads, offsets))
             arr[i] = _Job(reads.ctypes.data if reads.size else None, offsets.ctypes.data,
                           offsets.size - 1, k, m, lo, hi)
+        return keep, arr
+
+    def count_batch(self, jobs, copy: bool = True) -> list[CountResult]:
+        """jobs: sequence of (reads, offsets, k, m, lo, hi) host arrays."""
+        keep, arr = self._jobs(jobs)
         outs = (_Result * max(len(jobs), 1))()
         self._check(self.lib.hsk_count_batch(self.h, arr, len(jobs), outs))
         return [_host_result(outs[i], copy) for i in range(len(jobs))]
+
+    def autotune(self, jobs, max_trials: int = 16) -> dict:
+        """Tune the batched/served parameters on sample jobs (see hsk_autotune)."""
+        keep, arr = self._jobs(jobs)
+        r = _TuneResult()
+        self._check(self.lib.hsk_autotune(self.h, arr, len(jobs), max_trials, C.byref(r)))
+        return {f: getattr(r, f) for f, _ in _TuneResult._fields_}
+
+    def tune_set(self, **params):
+        """Put batched/served parameters in force (missing ones keep their value)."""
+        cur = self.tune_current()
+        cur.update(params)
+        r = _TuneResult(**{f: cur[f] for f, _ in _TuneResult._fields_})
+        self._check(self.lib.hsk_tune_set(self.h, C.byref(r)))
+
+    def tune_current(self) -> dict:
+        """The batched/served parameters in force on this context."""
+        r = _TuneResult()
+        self._check(self.lib.hsk_tune_current(self.h, C.byref(r)))
+        return {f: getattr(r, f) for f, _ in _TuneResult._fields_}
 
     # ---- served form ----------------------------------------------------------
     def submit(self, reads, offsets, k: int, m: int, lo: int, hi: int) -> int:

@@ -175,6 +175,11 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
             return HSK_ECUDA;
         }
         c->budget = cfg.hbm_budget ? cfg.hbm_budget : (size_t)(free_b * 0.9);
+        if (cfg.tune_cache) {
+            c->tune_path = cfg.tune_cache;
+            c->cfg.tune_cache = nullptr;  // the caller's string is not kept
+            hsk_tune_load(c);
+        }
         c->host_res.set_pinned(true);  // hsk_count's results: reused from call to call
         c->allocated = HSK_SMALL_BYTES;
         char* s = (char*)c->small;
@@ -212,6 +217,24 @@ extern "C" void hsk_destroy(hsk_ctx* c) {
 }
 
 extern "C" const char* hsk_last_error(hsk_ctx* c) { return c ? c->err_msg.c_str() : "null context"; }
+
+extern "C" int hsk_host_pin(void* p, uint64_t bytes) {
+    if (!p || bytes == 0) return HSK_EINVAL;
+    if (cudaHostRegister(p, (size_t)bytes, cudaHostRegisterDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return HSK_ECUDA;
+    }
+    return HSK_OK;
+}
+
+extern "C" int hsk_host_unpin(void* p) {
+    if (!p) return HSK_EINVAL;
+    if (cudaHostUnregister(p) != cudaSuccess) {
+        cudaGetLastError();
+        return HSK_ECUDA;
+    }
+    return HSK_OK;
+}
 
 // test hook: make the n-th following device allocation fail (-1 = never)
 extern "C" int hsk_debug_fail_alloc_after(hsk_ctx* c, int n) {
@@ -360,7 +383,8 @@ uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k) {
     if (n_bases < (1ull << 22)) return 256;
     // 128-bit keys: the on-chip sort holds half as many keys per sub-segment,
     // so large jobs need twice the groups
-    return (k > 32 && c->cfg.local_sort) ? 8192 : 4096;
+    const uint32_t B = (k > 32 && c->cfg.local_sort) ? 8192 : 4096;
+    return c->tune.plain_bucket_shift ? std::max<uint32_t>(256, B >> c->tune.plain_bucket_shift) : B;
 }
 
 static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, SmParams& P) {
@@ -872,7 +896,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
         if (nk == 0) continue;
         if (c->cfg.local_sort) {
             // groups of about a third of the on-chip capacity per top digit
-            const uint64_t per_group = 256ull * local_cap(kw) / 3;
+            const uint64_t per_group = 256ull * local_cap(kw) / (c->tune.group_div ? c->tune.group_div : 3);
             const uint32_t C_want = (uint32_t)std::min<uint64_t>(ch.second - ch.first,
                                                                  std::max<uint64_t>(1, nk / per_group));
             NvtxRange r("S4-S5 on-chip sort and count");

@@ -288,11 +288,16 @@ struct hsk_ctx {
 
     // tuned parameters (0 = built-in default); see hsk_tune.cu
     struct Tune {
-        uint32_t group_div = 0;        // bucket-group keys = 256 x on-chip capacity / group_div
-        uint64_t pack_bases = 0;       // bases of one pack at most
-        uint64_t pack_small = 0;       // sets with more bases run alone
-        int slots = 0;                 // serving slots
+        uint32_t group_div = 0;          // bucket-group keys = 256 x on-chip capacity / group_div (default 3)
+        uint32_t plain_bucket_shift = 0; // large plain jobs use (4096 or 8192) >> shift buckets
+        uint64_t pack_bases = 0;         // bases of one pack at most (default 2^30)
+        uint64_t pack_small = 0;         // sets with more bases run alone (default 2^28)
+        int slots = 0;                   // serving slots (default 4)
     } tune;
+    std::mutex tune_mu;
+    std::string tune_path;               // cache file of tuned parameters ("" = none)
+    std::vector<std::pair<std::string, Tune>> tuned;  // (class key, parameters)
+    bool tuning = false;                 // hsk_autotune is running its trials
 
     void* h_pin = nullptr;
     size_t h_pin_cap = 0;
@@ -398,3 +403,9 @@ int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, ui
                       int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st, DevBuf& d_reads,
                       DevBuf& d_offsets, HostResult& HR);
 void hsk_serve_shutdown(hsk_ctx* c);
+void hsk_serve_set_tune(hsk_ctx* c);  // the context's parameters to its serving slots
+// autotuner (hsk_tune.cu)
+std::string hsk_tune_class(const hsk_job* jobs, uint32_t n);
+void hsk_tune_load(hsk_ctx* c);
+bool hsk_tune_lookup(hsk_ctx* c, const std::string& key, hsk_ctx::Tune* out);
+void hsk_tune_apply(hsk_ctx* c, const hsk_ctx::Tune& t);

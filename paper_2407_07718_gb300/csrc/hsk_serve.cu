@@ -281,6 +281,12 @@ static int serve_start(hsk_ctx* c) {
     return HSK_OK;
 }
 
+void hsk_serve_set_tune(hsk_ctx* c) {
+    if (!c || !c->serve) return;
+    std::lock_guard<std::mutex> g(c->serve->mu);
+    for (hsk_ctx* s : c->serve->slots) s->tune = c->tune;
+}
+
 void hsk_serve_shutdown(hsk_ctx* c) {
     if (!c || !c->serve) return;
     ServeState* S = c->serve;
@@ -437,6 +443,10 @@ extern "C" int hsk_count_batch(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs,
         c->batch_res.clear();
         c->batch_res.resize(n_jobs);
         if (n_jobs == 0) return HSK_OK;
+        if (c->cfg.autotune && !c->tuning) {  // parameters recorded for this class of mix
+            hsk_ctx::Tune t;
+            if (hsk_tune_lookup(c, hsk_tune_class(jobs, n_jobs), &t)) hsk_tune_apply(c, t);
+        }
         TRY(serve_start(c));
         ServeState* S = c->serve;
         // Largest job first (longest-processing-time order): with the slots
