@@ -269,7 +269,7 @@ def bench_batched(hsk, device: int, n_sets: int, scale: float, tune_trials: int 
         batch_r = ctx.count_batch(jobs, copy=False)
         batch_s = time.perf_counter() - t0
         p1 = ctx.pack_stats()
-        packs = {key: p1[key] - p0[key] for key in p1}
+        packs = {key: (p1[key] - p0[key]) if isinstance(p1[key], int) else p1[key] for key in p1}
     for a, b in zip(plain_r, batch_r):
         assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct, b.extra["n_pairs"])
     del jobs
@@ -321,7 +321,7 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
     lat, plain_lat = [], []
     rate = None
     tuned = None
-    packs = {"passes": 0, "sets": 0, "alone": 0}
+    packs = {"passes": 0, "sets": 0, "alone": 0, "failed_passes": 0, "last_failure": ""}
     with hsk.Context(device=device, hbm_budget=budget) as ctx:
         for bi, bparams in enumerate(blocks):
             t0 = time.perf_counter()
@@ -375,7 +375,7 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
             open_s += time.perf_counter() - t0
             p1 = ctx.pack_stats()
             for key in packs:
-                packs[key] += p1[key] - p0[key]
+                packs[key] = packs[key] + p1[key] - p0[key] if isinstance(p1[key], int) else p1[key]
             for a, b in zip(plain_r, res):
                 assert (a.n_windows, a.n_distinct, a.extra["n_pairs"]) == (b.n_windows, b.n_distinct,
                                                                           b.extra["n_pairs"])

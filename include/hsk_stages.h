@@ -144,6 +144,11 @@ int hsk_debug_wait_timeout(hsk_ctx* ctx, uint32_t spin_limit);
  * pass could not finish (a sub-segment too large for the on-chip sort) and
  * that were then counted alone.  NULL outputs are skipped. */
 int hsk_debug_pack_stats(hsk_ctx* ctx, uint64_t* passes, uint64_t* sets, uint64_t* alone);
+/* Packed passes that failed as a whole (their jobs were then counted alone,
+ * so results are unaffected): *failed_passes (may be NULL) receives their
+ * number, the return value the last one's reason ("" if none; owned by the
+ * context, valid until the next failure). */
+const char* hsk_debug_pack_failure(hsk_ctx* ctx, uint64_t* failed_passes);
 
 /* Self-check of the host block pool that holds the batched and served forms'
  * results (size classes, best-fit reuse, the cap on kept blocks, arrays

@@ -112,6 +112,7 @@ def load():
             "hsk_launch_count": ([], u64),
             "hsk_sort_keys_noalloc": ([P, u64, i32, i32, P], i32),
             "hsk_debug_pack_stats": ([P, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
+            "hsk_debug_pack_failure": ([P, C.POINTER(u64)], C.c_char_p),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -197,19 +198,23 @@ def _summary(r: _Result) -> CountResult:
                        extra={"n_pairs": int(r.n_pairs)})
 
 
-def _host_result(r: _Result, copy: bool = True) -> CountResult:
-    if not copy:
+def _host_result(r: _Result, copy=True) -> CountResult:
+    """copy=True: numpy copies of the arrays; False: scalars only; "view":
+    numpy views of the library's host arrays, valid only while the result is
+    (until the next call on the context, or the ticket's release)."""
+    if copy is False:
         return _summary(r)
+    take = (lambda a: a) if copy == "view" else (lambda a: a.copy())
     n, kw = int(r.n_pairs), int(r.key_words)
     if n:
-        kmers = np.ctypeslib.as_array(C.cast(r.kmers, C.POINTER(C.c_uint64)), shape=(n * kw,)).copy()
-        counts = np.ctypeslib.as_array(C.cast(r.counts, C.POINTER(C.c_uint32)), shape=(n,)).copy()
+        kmers = take(np.ctypeslib.as_array(C.cast(r.kmers, C.POINTER(C.c_uint64)), shape=(n * kw,)))
+        counts = take(np.ctypeslib.as_array(C.cast(r.counts, C.POINTER(C.c_uint32)), shape=(n,)))
     else:
         kmers = np.zeros(0, np.uint64)
         counts = np.zeros(0, np.uint32)
     if kw == 2:
         kmers = kmers.reshape(n, 2)
-    hist = np.ctypeslib.as_array(C.cast(r.hist, C.POINTER(C.c_uint64)), shape=(int(r.hist_len),)).copy()
+    hist = take(np.ctypeslib.as_array(C.cast(r.hist, C.POINTER(C.c_uint64)), shape=(int(r.hist_len),)))
     return CountResult(kmers, counts, hist, int(r.n_windows), int(r.n_distinct), int(r.max_count), kw,
                        int(r.n_chunks), int(r.n_supermers), float(r.device_ms))
 
@@ -433,9 +438,11 @@ class Context:
     def pack_stats(self) -> dict:
         """Packed passes of the batched/served forms so far: passes, jobs they
         held, and jobs among those counted again alone."""
-        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        a, b, c, f = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
         self._check(self.lib.hsk_debug_pack_stats(self.h, C.byref(a), C.byref(b), C.byref(c)))
-        return {"passes": a.value, "sets": b.value, "alone": c.value}
+        msg = self.lib.hsk_debug_pack_failure(self.h, C.byref(f)).decode()
+        return {"passes": a.value, "sets": b.value, "alone": c.value, "failed_passes": f.value,
+                "last_failure": msg}
 
     def last_overflow(self) -> int:
         """Keys of the last call that went through the global radix passes

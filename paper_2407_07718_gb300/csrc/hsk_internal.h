@@ -146,6 +146,13 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
                        uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
                        uint32_t* max_count, uint64_t* n_distinct, const uint32_t* grp_set, uint32_t* claim,
                        int* err, int num_sms, cudaStream_t st);
+// heavy-hitter sub-segments of 64-bit keys (listed by the first on-chip pass):
+// each folded into a shared-memory (k-mer, count) table; too many distinct
+// keys -> listed again in ov_list for the global path
+void launch_heavy_count(const uint64_t* sub_off, const uint32_t* list, uint32_t n_list, void* keys,
+                        uint32_t* kcount, uint32_t* kc, uint32_t* ov_list, uint64_t* ov_stats, uint32_t lo,
+                        uint32_t hi, uint64_t* hist, uint32_t hist_len, uint32_t* max_count, uint64_t* n_distinct,
+                        const uint32_t* grp_set, uint32_t* claim, int* err, int num_sms, cudaStream_t st);
 void launch_compact(const uint64_t* sub_off, const uint32_t* kc, const uint64_t* out_off, uint32_t n_sub,
                     int key_words, const void* keys, const uint32_t* kcount, void* out_keys, uint32_t* out_counts,
                     uint64_t out_cap, int* err, int grid, cudaStream_t st);

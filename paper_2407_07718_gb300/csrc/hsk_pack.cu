@@ -260,12 +260,13 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         memcpy(tseg.data() + nt, grp_set.data(), (size_t)C * 4);  // group -> set after the tile map
         TRY(hsk_ensure(c, c->keys, nk * kb, false));
         TRY(hsk_ensure(c, c->alt, nk * 4, false));
-        const size_t t32b = 4 * NS * 4;
+        const size_t t32b = (5 * NS * 4 + 7) & ~(size_t)7;
         TRY(hsk_ensure(c, c->loc_tab, t32b + (3 * NS + 2) * 8, false));
         uint32_t* sub_cnt = (uint32_t*)c->loc_tab.p;
         uint32_t* kcv = sub_cnt + NS;
         uint32_t* ov_list = kcv + NS;
         uint32_t* ov_list2 = ov_list + NS;
+        uint32_t* ov_list3 = ov_list2 + NS;
         uint64_t* sub_off = (uint64_t*)((char*)c->loc_tab.p + t32b);
         uint64_t* cursor = sub_off + NS + 1;
         uint64_t* kc_off = cursor + NS;
@@ -291,24 +292,23 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         launch_part(1, SMR.records, d_rbase, d_tbase, d_tseg, (uint32_t)nt, k, shift0, ctr, nullptr, cursor,
                     sub_off + 1, c->keys.p, c->d_err, expand_grid(c->num_sms), st);
         CK(cudaGetLastError());
-        // S4/S5 on chip, statistics per set; a second pass for the larger sub-segments
-        CK(cudaMemsetAsync(c->d_nlocal, 0, 40, st));
+        // S4/S5 on chip, statistics per set; the larger sub-segments take the
+        // second pass and the heavy-hitter k-mer lists (as in the plain path)
+        CK(cudaMemsetAsync(c->d_nlocal, 0, 56, st));
         TRY(hsk_next_counter(c, st, &ctr));
         launch_local_sort(sub_off, nullptr, (uint32_t)NS, false, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
                           ov_list, c->d_ovstats, lo, hi, (uint64_t*)c->hist.p, H, d_max, d_distinct, d_grp_set, ctr,
                           c->d_err, c->num_sms, st);
         CK(cudaGetLastError());
-        uint64_t st5[5] = {0, 0, 0, 0, 0};
-        CK(cudaMemcpyAsync(st5, c->d_nlocal, 24, cudaMemcpyDeviceToHost, st));
+        uint64_t st3[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync(st3, c->d_nlocal, sizeof(st3), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const uint32_t n_ov1 = (uint32_t)(st5[1] & 0xFFFFFFFFull);
-        if (n_ov1) {
-            TRY(hsk_next_counter(c, st, &ctr));
-            launch_local_sort(sub_off, ov_list, n_ov1, true, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
-                              ov_list2, c->d_ovstats + 2, lo, hi, (uint64_t*)c->hist.p, H, d_max, d_distinct,
-                              d_grp_set, ctr, c->d_err, c->num_sms, st);
-            CK(cudaGetLastError());
-        }
+        uint32_t* left = nullptr;
+        uint32_t n_ov = 0;
+        uint64_t ov_keys = 0;
+        TRY(hsk_local_overflow(c, sub_off, (uint32_t)(st3[1] & 0xFFFFFFFFull), ov_list, ov_list2, ov_list3, kw,
+                               shift0, c->keys.p, (uint32_t*)c->alt.p, kcv, lo, hi, (uint64_t*)c->hist.p, H, d_max,
+                               d_distinct, d_grp_set, st, &left, &n_ov, &ov_keys));
         TRY(hsk_next_epoch(c, st, &ep));
         TRY(hsk_next_counter(c, st, &ctr));
         launch_scan_u32(kcv, NS, kc_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
@@ -321,13 +321,11 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         CK(cudaMemcpyAsync(d_at, at.data(), (S + 1) * 8, cudaMemcpyHostToDevice, st));
         launch_gather_u64(kc_off, d_at, S + 1, d_poff, st);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(st5, c->d_nlocal, sizeof(st5), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(pair_off.data(), d_poff, (S + 1) * 8, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const uint32_t n_ov = (uint32_t)(st5[3] & 0xFFFFFFFFull);
-        if (n_ov) {  // sets with a sub-segment the on-chip sort could not take: counted again alone
+        if (n_ov) {  // sets with a sub-segment the on-chip steps could not take: counted again alone
             std::vector<uint32_t> ovs(n_ov);
-            CK(cudaMemcpyAsync(ovs.data(), ov_list2, (size_t)n_ov * 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(ovs.data(), left, (size_t)n_ov * 4, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             for (uint32_t s : ovs) redo[grp_set[s >> 8]] = 1;
         }
@@ -448,7 +446,7 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
 }
 
 int hsk_count_pack_host(hsk_ctx* c, PackSet* sets, uint32_t n_sets, int k, int m, uint32_t lo, uint32_t hi,
-                        cudaStream_t st) {
+                        cudaStream_t st, std::string* fail_msg) {
     const int kw = k <= 32 ? 1 : 2;
     std::vector<PackSet*> run;
     std::vector<uint64_t> nb;
@@ -471,6 +469,7 @@ int hsk_count_pack_host(hsk_ctx* c, PackSet* sets, uint32_t n_sets, int k, int m
     if (rc != HSK_OK) {
         // the pass failed as a whole: every set that took part is counted alone
         // (that also tells which set, if any, holds the fault)
+        if (fail_msg) *fail_msg = c->err_msg;
         for (PackSet* s : run) s->rc = HSK_PACK_REDO;
         cudaStreamSynchronize(st);
     }

@@ -31,5 +31,6 @@ uint64_t hsk_pack_group_keys(hsk_ctx* c, int key_words);
 // Count the sets (all with k, m, lo, hi) by one pass on stream st; each set's
 // rc and out are filled.  Sets the pass could not finish are counted alone.
 // Returns HSK_OK unless the context itself failed.
+// *fail_msg (may be NULL) receives the reason when the pass as a whole failed.
 int hsk_count_pack_host(hsk_ctx* c, PackSet* sets, uint32_t n_sets, int k, int m, uint32_t lo, uint32_t hi,
-                        cudaStream_t st);
+                        cudaStream_t st, std::string* fail_msg = nullptr);

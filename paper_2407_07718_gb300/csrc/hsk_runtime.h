@@ -270,7 +270,7 @@ struct hsk_ctx {
     uint64_t* d_nout = nullptr;
     uint64_t* d_ndesc = nullptr;
     uint64_t* d_nlocal = nullptr;   // distinct k-mers counted on chip
-    uint64_t* d_ovstats = nullptr;  // [0] low half: sub-segments sent to the global path, [1] their keys
+    uint64_t* d_ovstats = nullptr;  // per on-chip step: [2i] low half = sub-segments it listed, [2i+1] their keys
     uint32_t* counters = nullptr;
     uint32_t ctr_used = 0;
     uint32_t epoch = 0;
@@ -310,6 +310,8 @@ struct hsk_ctx {
     // packed passes run for this context's batched and served jobs, the sets
     // they held, and the sets among them counted again alone
     std::atomic<uint64_t> pack_passes{0}, pack_sets{0}, pack_redo{0};
+    std::atomic<uint64_t> pack_fail{0};  // passes that failed as a whole (their sets were counted alone)
+    std::string pack_fail_msg;           // the last such failure's reason (under tune_mu)
 
     // profiling: events at stage boundaries (stage id of the span that ends there)
     bool prof = false;
@@ -396,6 +398,11 @@ int hsk_plan_chunks(hsk_ctx* c, const Supermers& S, int key_words, std::vector<s
 int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S, cudaStream_t st,
                   InputPipe* pipe, const SetMap* sets = nullptr);
 uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k);
+int hsk_local_overflow(hsk_ctx* c, const uint64_t* sub_off, uint32_t n_ov1, uint32_t* ov_list, uint32_t* ov_list2,
+                       uint32_t* ov_list3, int kw, int shift0, void* keys, uint32_t* kcount, uint32_t* kcv,
+                       uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t H, uint32_t* d_max, uint64_t* d_distinct,
+                       const uint32_t* grp_set, cudaStream_t st, uint32_t** left, uint32_t* n_left,
+                       uint64_t* left_keys);
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
                   DevResult& R, InputPipe* pipe = nullptr);

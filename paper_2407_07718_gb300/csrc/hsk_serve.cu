@@ -219,9 +219,16 @@ static void worker_main(hsk_ctx* parent, ServeState* S, int slot) {
                 ps[i].out = &hrs[i];
             }
             const hsk_job& j0 = group[0]->job;
+            std::string fail;
             const int rc = hsk_guarded(c, [&]() -> int {
-                return hsk_count_pack_host(c, ps.data(), (uint32_t)ps.size(), j0.k, j0.m, j0.lo, j0.hi, c->stream);
+                return hsk_count_pack_host(c, ps.data(), (uint32_t)ps.size(), j0.k, j0.m, j0.lo, j0.hi, c->stream,
+                                           &fail);
             });
+            if (!fail.empty()) {
+                parent->pack_fail.fetch_add(1);
+                std::lock_guard<std::mutex> g2(parent->tune_mu);
+                parent->pack_fail_msg = fail;
+            }
             for (size_t i = 0; i < group.size(); ++i) {
                 rcs[i] = rc != HSK_OK ? rc : ps[i].rc;
                 errs[i] = rc != HSK_OK ? c->err_msg : ps[i].err;
@@ -503,4 +510,11 @@ extern "C" int hsk_debug_pack_stats(hsk_ctx* c, uint64_t* passes, uint64_t* sets
     if (sets) *sets = c->pack_sets.load();
     if (alone) *alone = c->pack_redo.load();
     return HSK_OK;
+}
+
+extern "C" const char* hsk_debug_pack_failure(hsk_ctx* c, uint64_t* failed_passes) {
+    if (!c) return "";
+    if (failed_passes) *failed_passes = c->pack_fail.load();
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    return c->pack_fail_msg.c_str();
 }

@@ -901,6 +901,161 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
 }
 
 // ---------------------------------------------------------------------------
+// heavy-hitter sub-segments (64-bit keys): the k-mer list of a task
+// ---------------------------------------------------------------------------
+// Sec. 3.5: a task whose size exceeds a constant times the mean task size
+// holds heavy hitters (many copies of a few k-mers, from genomic repeats);
+// such a task is transformed into a k-mer list -- one (k-mer, count) tuple
+// per distinct k-mer -- instead of being counted the normal way.  Here the
+// tasks are the sub-segments, a heavy one is one over the first pass's
+// on-chip capacity (about three times the mean sub-segment), and since a
+// sub-segment holds every copy of each of its k-mers, its k-mer list is the
+// exact count: one CTA folds the sub-segment's keys into a shared-memory table
+// (open addressing, a 64-bit compare-and-swap claims a slot, an atomic add
+// counts), then every slot is one distinct k-mer with its count, which goes to
+// the histogram and the [lo, hi] filter like any run.  A sub-segment whose
+// distinct keys would fill the table past HV_FILL is listed for the global
+// radix path instead.
+constexpr int HV_NT = 1024;
+constexpr int HV_SLOTS = 16384;               // 128 KB keys + 64 KB counts
+constexpr int HV_PF = 8;                      // keys per thread loaded ahead in one round
+constexpr int HV_FILL = HV_SLOTS * 7 / 8;     // most distinct keys held before giving up
+constexpr int HV_LIST = HV_FILL + HV_NT;      // claimed slots (each thread claims at most one past HV_FILL)
+static_assert(HV_LIST < HV_SLOTS, "the table never fills: every probe sequence ends");
+constexpr u64 HV_EMPTY = ~0ULL;               // never a canonical key (all-T's reverse complement is smaller)
+
+size_t heavy_smem_bytes() { return (size_t)HV_SLOTS * (8 + 4) + (size_t)HV_LIST * 2; }
+
+__global__ void __launch_bounds__(HV_NT, 1) k_heavy_count(const u64* __restrict__ sub_off,
+                                                          const uint32_t* __restrict__ list, uint32_t n_list,
+                                                          u64* keys, uint32_t* __restrict__ kcount,
+                                                          uint32_t* __restrict__ kc, uint32_t* __restrict__ ov_list,
+                                                          unsigned long long* ov_stats, uint32_t lo, uint32_t hi,
+                                                          u64* __restrict__ hist, uint32_t hist_len,
+                                                          uint32_t* max_count, unsigned long long* n_distinct,
+                                                          const uint32_t* __restrict__ grp_set, uint32_t* claim,
+                                                          int* err) {
+    extern __shared__ __align__(16) unsigned char smem_hv[];
+    u64* tk = reinterpret_cast<u64*>(smem_hv);
+    uint32_t* tc = reinterpret_cast<uint32_t*>(tk + HV_SLOTS);
+    uint16_t* s_slot = reinterpret_cast<uint16_t*>(tc + HV_SLOTS);  // slots claimed for this task
+    __shared__ uint32_t s_used, s_fail, s_kept, s_next, s_max;
+    __shared__ unsigned long long s_distinct;
+    const int tid = threadIdx.x, lane = tid & 31;
+    // the table starts empty once; each task resets only the slots it claimed
+    for (int i = tid; i < HV_SLOTS; i += HV_NT) {
+        tk[i] = HV_EMPTY;
+        tc[i] = 0;
+    }
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s_next = atomicAdd(claim, 1u);
+            s_used = 0;
+            s_fail = 0;
+            s_kept = 0;
+            s_max = 0;
+            s_distinct = 0;
+        }
+        __syncthreads();
+        const uint32_t si = s_next;
+        if (si >= n_list) break;
+        const uint32_t s = list[si];
+        const u64 base = sub_off[s], n = sub_off[s + 1] - base;
+        const uint32_t set = grp_set ? grp_set[s >> 8] : 0u;
+        // fold the keys into the table, HV_PF keys per thread and round loaded
+        // ahead; the copies of a key within a warp are added by one lane
+        // (heavy hitters repeat inside a warp's keys)
+        for (u64 r0 = 0; r0 < n; r0 += (u64)HV_NT * HV_PF) {
+            if (__any_sync(0xffffffffu, *(volatile uint32_t*)&s_fail != 0)) break;
+            u64 kr[HV_PF];
+#pragma unroll
+            for (int j = 0; j < HV_PF; ++j) {
+                const u64 i = r0 + (u64)j * HV_NT + tid;
+                kr[j] = i < n ? keys[base + i] : HV_EMPTY;
+            }
+#pragma unroll
+            for (int j = 0; j < HV_PF; ++j) {
+                if (__any_sync(0xffffffffu, *(volatile uint32_t*)&s_fail != 0)) break;  // checked before every claim
+                const u64 key = kr[j];
+                const uint32_t peers = __match_any_sync(0xffffffffu, key);
+                if (key == HV_EMPTY || lane != __ffs(peers) - 1) continue;
+                const uint32_t copies = (uint32_t)__popc(peers);
+                uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ULL) >> 50) & (HV_SLOTS - 1);  // 14 bits
+                for (int probe = 0; probe < HV_SLOTS; ++probe) {
+                    const u64 prev = atomicCAS(reinterpret_cast<unsigned long long*>(&tk[h]), HV_EMPTY, key);
+                    if (prev == HV_EMPTY || prev == key) {
+                        atomicAdd(&tc[h], copies);
+                        if (prev == HV_EMPTY) {
+                            const uint32_t q = atomicAdd(&s_used, 1u);
+                            if (q < (uint32_t)HV_LIST) s_slot[q] = (uint16_t)h;
+                            if (q + 1 > (uint32_t)HV_FILL) s_fail = 1;
+                        }
+                        break;
+                    }
+                    h = (h + 1) & (HV_SLOTS - 1);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t used = s_used < (uint32_t)HV_LIST ? s_used : (uint32_t)HV_LIST;
+        const bool fail = s_fail != 0;
+        // every claimed slot is one distinct k-mer of the task with its exact
+        // count (or, after a failure, is only cleared)
+        u64* hset = hist + (u64)set * hist_len;
+        uint32_t my_max = 0;
+        unsigned long long my_d = 0;
+        for (uint32_t q = tid; q < used; q += HV_NT) {
+            const uint32_t slot = s_slot[q];
+            const uint32_t cnt = tc[slot];
+            const u64 key = tk[slot];
+            tk[slot] = HV_EMPTY;
+            tc[slot] = 0;
+            if (fail) continue;
+            ++my_d;
+            my_max = cnt > my_max ? cnt : my_max;
+            const uint32_t b = cnt < hist_len - 1 ? cnt : hist_len - 1;
+            atomicAdd(reinterpret_cast<unsigned long long*>(hset + b), 1ULL);
+            if (cnt >= lo && cnt <= hi) {
+                const uint32_t p = atomicAdd(&s_kept, 1u);
+                keys[base + p] = key;  // the task's own range: every key is in the table already
+                kcount[base + p] = cnt;
+            }
+        }
+        if (fail) {  // too many distinct keys: the global path takes it
+            if (tid == 0) {
+                kc[s] = 0;
+                ov_list[atomicAdd(reinterpret_cast<unsigned int*>(ov_stats), 1u)] = s;
+                atomicAdd(ov_stats + 1, (unsigned long long)n);
+            }
+            continue;
+        }
+        if (my_d) atomicAdd(&s_distinct, my_d);
+        if (my_max) atomicMax(&s_max, my_max);
+        __syncthreads();
+        if (tid == 0) {
+            kc[s] = s_kept;
+            if (s_distinct) atomicAdd(n_distinct + set, s_distinct);
+            if (s_max) atomicMax(max_count + set, s_max);
+        }
+    }
+}
+
+void launch_heavy_count(const uint64_t* sub_off, const uint32_t* list, uint32_t n_list, void* keys,
+                        uint32_t* kcount, uint32_t* kc, uint32_t* ov_list, uint64_t* ov_stats, uint32_t lo,
+                        uint32_t hi, uint64_t* hist, uint32_t hist_len, uint32_t* max_count, uint64_t* n_distinct,
+                        const uint32_t* grp_set, uint32_t* claim, int* err, int num_sms, cudaStream_t st) {
+    if (n_list == 0) return;
+    count_launch();
+    const size_t dyn = heavy_smem_bytes();
+    cudaFuncSetAttribute(k_heavy_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const unsigned g = n_list < (uint32_t)num_sms ? n_list : (unsigned)num_sms;
+    k_heavy_count<<<g, HV_NT, dyn, st>>>((const u64*)sub_off, list, n_list, (u64*)keys, kcount, kc, ov_list,
+                                         (unsigned long long*)ov_stats, lo, hi, (u64*)hist, hist_len, max_count,
+                                         (unsigned long long*)n_distinct, grp_set, claim, err);
+}
+
+// ---------------------------------------------------------------------------
 // kept pairs -> output; listed sub-segments -> one array
 // ---------------------------------------------------------------------------
 // Warp w copies the kc[s] kept pairs of sub-segment s (from its range start)

@@ -150,15 +150,15 @@ def test_repeated_calls_reuse_the_arena(hsk, tiny):
 @pytest.mark.parametrize("case", ["tiny", "one_bucket", "k55", "repeats", "small_hist"])
 def test_on_chip_and_global_paths_agree(hsk, tiny, case):
     """The on-chip sub-segment sort and the global radix passes give the same
-    bytes; one bucket forces sub-segments over the on-chip capacity, so the
-    fallback path runs next to the on-chip one."""
+    bytes; one bucket forces sub-segments over the on-chip sort's capacity,
+    which the heavy-hitter path then counts on chip as k-mer lists."""
     kw = dict(hist_len=65536)
     k, m, lo, hi = 31, 17, 2, 1000
     if case == "tiny":
         reads, offs = tiny.reads, tiny.offsets
     elif case == "one_bucket":
-        # 2.4 M keys in one bucket: 256 sub-segments of ~9 K keys, the largest
-        # past both on-chip capacities, so all three paths run
+        # 2.4 M keys in one bucket: 256 sub-segments of ~9 K keys, past the
+        # first pass's capacity: heavy-hitter tasks
         reads, offs = tiny.reads, tiny.offsets
         kw["n_buckets"] = 1
     elif case == "k55":
@@ -184,7 +184,7 @@ def test_on_chip_and_global_paths_agree(hsk, tiny, case):
         ga = a.count(reads, offs, k, m, lo, hi)
         gb = b.count(reads, offs, k, m, lo, hi)
         if case == "one_bucket":
-            assert a.last_overflow() > 0  # the global fallback ran next to the on-chip passes
+            assert a.last_overflow() == 0  # every heavy task was counted on chip
     assert_same_result(ga, want, f"{case} on-chip")
     assert_same_result(gb, want, f"{case} global")
 
@@ -217,3 +217,36 @@ def test_bounded_wait_gives_up_and_context_stays_usable(hsk, tiny, limit):
         assert ctx.wait_timeout(limit) == -4  # HSK_ETIMEOUT
         assert_same_result(ctx.count(reads, offs, 31, 17, 2, 1000), want, "after a timed-out wait")
         assert ctx.wait_timeout(limit) == -4
+
+
+def test_heavy_hitter_task_is_counted_on_chip(hsk):
+    """Sec. 3.5: a task far above the mean size (here: one k-mer with ~20,000
+    copies) is turned into a k-mer list on chip; nothing goes to the global
+    radix path, and the result is the oracle's."""
+    strs = ["A" * 20_000, "ACGTTGCA" * 40, "C" * 5_000]
+    offs = np.zeros(len(strs) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(x) for x in strs])
+    reads = np.frombuffer("".join(strs).encode(), np.uint8).copy()
+    want = oracle.count(reads, offs, 31, 2, 100000)
+    with hsk.Context() as ctx:
+        got = ctx.count(reads, offs, 31, 17, 2, 100000)
+        assert ctx.last_overflow() == 0
+    assert_same_result(got, want, "poly-A")
+
+
+def test_task_with_too_many_distinct_keys_takes_the_global_path(hsk):
+    """A heavy task whose distinct keys overfill the on-chip k-mer list (20,000
+    distinct 31-mers sharing their top digit, each twice) goes to the global
+    radix passes; the result is the oracle's."""
+    rng = np.random.default_rng(3)
+    body = rng.choice(np.array(list("ACGT")), size=(20_000, 27))
+    strs = ["AAAA" + "".join(r) for r in body]
+    strs = strs + strs
+    offs = np.zeros(len(strs) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(x) for x in strs])
+    reads = np.frombuffer("".join(strs).encode(), np.uint8).copy()
+    want = oracle.count(reads, offs, 31, 2, 1000)
+    with hsk.Context() as ctx:
+        got = ctx.count(reads, offs, 31, 17, 2, 1000)
+        assert ctx.last_overflow() == 40_000
+    assert_same_result(got, want, "distinct-heavy")

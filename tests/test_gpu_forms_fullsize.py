@@ -1,0 +1,74 @@
+"""The batched form on all 256 sets of the batched workload and the served
+form on all 2,000 requests of the served workload, each job's result checked
+bit for bit against the oracle's run on that job alone (the digests of
+tests/golden/fullsize_digests.json, written by the oracle only): every scalar,
+the SHA-256 of the (k-mer, count) pairs and of the histogram.  The SHA-256 of
+each job's simulated reads is checked too, so a simulator that drifted between
+machines fails as such.
+
+The served requests are simulated and submitted in blocks of 250 (about 17 GB
+of host input each), all of a block's tickets queued at once so that the
+slots pack them; results are hashed while their tickets are held, then
+released."""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import datagen
+import digests
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+_POOL = ThreadPoolExecutor(max_workers=16)
+
+
+def _make(fn, params):
+    def one(p):
+        rs = fn(*p)
+        return rs, digests.reads_sha(rs.reads, rs.offsets)
+    return list(_POOL.map(one, params))
+
+
+def _check_all(results, wants, labels):
+    def one(i):
+        digests.check(results[i], wants[i], labels[i])
+        return True
+    assert all(_POOL.map(one, range(len(results))))
+
+
+def test_batched_form_256_sets_bit_exact(hsk):
+    gold = digests.golden()
+    params = datagen.batched_set_params(n_sets=256)
+    made = _make(datagen.batched_set, params)
+    labels = [f"batched/{i}" for i in range(len(made))]
+    wants = [gold[lb] for lb in labels]
+    for (rs, sha), w, lb in zip(made, wants, labels):
+        assert sha == w["reads_sha256"], f"{lb}: the simulator produced other reads"
+    jobs = [(rs.reads, rs.offsets, rs.k, rs.m, rs.lo, rs.hi) for rs, _ in made]
+    with hsk.Context() as ctx:
+        got = ctx.count_batch(jobs, copy="view")
+        _check_all(got, wants, labels)
+        stats = ctx.pack_stats()
+    assert stats["sets"] > 0, stats
+
+
+def test_served_form_2000_requests_bit_exact(hsk):
+    gold = digests.golden()
+    params = datagen.served_request_params(n=2000)
+    block = 250
+    with hsk.Context() as ctx:
+        for b0 in range(0, len(params), block):
+            made = _make(datagen.served_request, params[b0:b0 + block])
+            labels = [f"served/{b0 + i}" for i in range(len(made))]
+            wants = [gold[lb] for lb in labels]
+            for (rs, sha), w, lb in zip(made, wants, labels):
+                assert sha == w["reads_sha256"], f"{lb}: the simulator produced other reads"
+                assert (rs.k, rs.m, rs.lo, rs.hi) == (w["k"], w["m"], w["lo"], w["hi"]), lb
+            tickets = [ctx.submit(rs.reads, rs.offsets, rs.k, rs.m, rs.lo, rs.hi) for rs, _ in made]
+            got = [ctx.wait(t, copy="view") for t in tickets]
+            _check_all(got, wants, labels)
+            for t in tickets:
+                ctx.release(t)
+            del made, got
+        assert ctx.pack_stats()["sets"] > 0

@@ -11,13 +11,19 @@ set:
     sum over [lo, hi] of hist = n_pairs;
   * sampled output pairs: their counts equal the oracle's;
   * sampled k-mers of the input, present or not in the output: present exactly
-    when the oracle's count lies in [lo, hi], and then with that count.
+    when the oracle's count lies in [lo, hi], and then with that count;
+  * and the whole result, bit for bit: the SHA-256 of the (k-mer, count) pairs
+    and of the histogram, and every scalar, against the oracle's full-size run
+    recorded in tests/golden/fullsize_digests.json (written by the oracle alone;
+    the SHA-256 of the simulated reads is checked first, so a simulator that
+    drifted between machines fails as such, not as counting).
 """
 import numpy as np
 import pytest
 
 import datagen
 import oracle
+import digests
 from gpu_util import dev, dev_u64
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -106,3 +112,12 @@ def test_sampled_input_kmers_present_iff_in_range(case):
     assert np.array_equal(got.counts[pos[found]].astype(np.uint64), want[found]), name
     # both outcomes were sampled
     assert found.any() and (~found).any(), (name, int(found.sum()), found.size)
+
+
+def test_bit_exact_against_the_oracles_full_size_run(case):
+    name, rs, got = case
+    want = digests.golden()[name]
+    assert digests.reads_sha(rs.reads, rs.offsets) == want["reads_sha256"], \
+        f"{name}: the simulator produced other reads than when the digests were written"
+    assert (rs.k, rs.m, rs.lo, rs.hi) == (want["k"], want["m"], want["lo"], want["hi"])
+    digests.check(got, want, name)

@@ -75,21 +75,36 @@ def test_count_batch_packs_small_sets_bit_exact(hsk, k, m, lo, hi):
             assert_same_result(g, wants[i], f"k={k} set {i} (permuted)")
 
 
-def test_pack_hands_back_a_set_too_repetitive_for_the_chip(hsk):
-    """A poly-A read makes one k-mer with ~20,000 copies: its sub-segment is
-    over the on-chip capacity, so that set is counted again alone; the other
-    sets of the pass keep their packed results."""
+def _distinct_heavy_set(n=20_000, seed=3):
+    """n distinct 31-mers that all start with AAAA, each read twice: their
+    canonical keys share the top digit, so one sub-segment holds all of them --
+    more distinct keys than the heavy-hitter table holds."""
+    rng = np.random.default_rng(seed)
+    acgt = np.array(list("ACGT"))
+    body = rng.choice(acgt, size=(n, 27))
+    reads = ["AAAA" + "".join(r) for r in body]
+    return _pack(reads + reads)
+
+
+def test_pack_handles_heavy_hitters_and_hands_back_what_it_cannot(hsk):
+    """A poly-A read makes one k-mer with ~20,000 copies: its sub-segment is a
+    heavy-hitter task (over the on-chip capacity), folded into a k-mer list on
+    chip inside the pass.  A set whose one sub-segment holds more distinct
+    keys than that table is handed back and counted alone.  Every set stays
+    bit-exact."""
     jobs = _small_jobs(31, 17, 2, 100000, 12, 7)
     r, o = _pack(["A" * 20_000, "ACGT" * 50])
     jobs.insert(5, (r, o, 31, 17, 2, 100000))
+    r2, o2 = _distinct_heavy_set()
+    jobs.insert(9, (r2, o2, 31, 17, 2, 100000))
     wants = _oracle(jobs)
     with hsk.Context() as ctx:
         got = ctx.count_batch(jobs)
         stats = ctx.pack_stats()
     for i, (g, w) in enumerate(zip(got, wants)):
         assert_same_result(g, w, f"set {i}")
-    assert stats["alone"] >= 1, stats
     assert got[5].max_count == 20_000 - 31 + 1
+    assert stats["alone"] == 1, stats  # the distinct-heavy set only
 
 
 def test_packed_results_equal_plain_calls(hsk):
