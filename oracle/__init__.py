@@ -17,6 +17,8 @@ Functions and the passage each follows:
   windows        -- Sec. 3.2 (hash-scored minimizer via the monotone deque).
   supermers      -- Sec. 2.4 and Sec. 3.2 (supermers), Sec. 3.4 (tasks).
   sort_u64       -- Sec. 3.1 (the sort alone is std::sort).
+  count_ext      -- Sec. 3.3.2 (extension information: each kept k-mer's
+                    occurrences as (read, position)).
 """
 from __future__ import annotations
 
@@ -85,6 +87,8 @@ def _load():
             lib.oracle_supermers.argtypes = [P, P, u64, i32, i32, u64, u32, P, P, P, P]
             lib.oracle_supermers.restype = u64
             lib.oracle_sort_u64.argtypes = [P, u64]
+            lib.oracle_count_ext.argtypes = [P, P, u64, i32, u32, u32, P, P, P, P, P]
+            lib.oracle_count_ext.restype = C.c_int64
             lib.oracle_fmix64.argtypes = [u64]
             lib.oracle_fmix64.restype = u64
             lib.oracle_fmix32.argtypes = [u32]
@@ -206,6 +210,41 @@ def supermers(reads, offsets, k: int, m: int, n_buckets: int, seed: int = DEFAUL
     ns = lib.oracle_supermers(_ptr(reads), _ptr(offsets), offsets.size - 1, k, m, seed,
                               n_buckets, _ptr(sp), _ptr(sn), _ptr(sb), _ptr(bk))
     return sp[:ns], sn[:ns], sb[:ns], bk
+
+
+@dataclass
+class ExtResult:
+    kmers: np.ndarray       # (n,) uint64 or (n, 2) uint64 {lo, hi}, ascending
+    counts: np.ndarray      # (n,) uint32
+    occ_offsets: np.ndarray  # (n + 1,) uint64: k-mer i's occurrences are [occ_offsets[i], occ_offsets[i+1])
+    occ_read: np.ndarray    # uint32 read index of each occurrence
+    occ_pos: np.ndarray     # uint32 position in the read (window start)
+    key_words: int = 1
+
+
+def count_ext(reads, offsets, k: int, lo: int, hi: int) -> ExtResult:
+    """Kept k-mers with their occurrences (read, position), Sec. 3.3.2."""
+    lib = _load()
+    reads, offsets = _as_inputs(reads, offsets)
+    n = offsets.size - 1
+    npairs = np.zeros(1, np.uint64)
+    no = lib.oracle_count_ext(_ptr(reads), _ptr(offsets), n, k, lo, hi, _ptr(npairs), None, None, None, None)
+    if no < 0:
+        raise ValueError("oracle_count_ext rejected its arguments")
+    kw = 1 if k <= 32 else 2
+    np_ = int(npairs[0])
+    kmers = np.zeros(max(np_ * kw, 1), np.uint64)
+    counts = np.zeros(max(np_, 1), np.uint32)
+    occ_read = np.zeros(max(no, 1), np.uint32)
+    occ_pos = np.zeros(max(no, 1), np.uint32)
+    lib.oracle_count_ext(_ptr(reads), _ptr(offsets), n, k, lo, hi, _ptr(npairs), _ptr(kmers), _ptr(counts),
+                         _ptr(occ_read), _ptr(occ_pos))
+    kmers, counts = kmers[: np_ * kw], counts[:np_]
+    if kw == 2:
+        kmers = kmers.reshape(np_, 2)
+    offs = np.zeros(np_ + 1, np.uint64)
+    offs[1:] = np.cumsum(counts, dtype=np.uint64)
+    return ExtResult(kmers, counts, offs, occ_read[:no], occ_pos[:no], kw)
 
 
 def sort_u64(keys: np.ndarray) -> np.ndarray:

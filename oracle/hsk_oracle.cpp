@@ -21,6 +21,8 @@
 //   * oracle_supermers  -- stage reference for supermers and buckets (Sec. 2.4,
 //                          Sec. 3.2, Sec. 3.4 tasks).
 //   * oracle_sort_u64   -- stage reference for the sort: std::sort (Sec. 3.1).
+//   * oracle_count_ext  -- extension information of the kept k-mers: every
+//                          occurrence's read and position (Sec. 3.3.2).
 //
 // Readings of the paper that these functions fix (the paper is silent on them):
 //   base code A=0 C=1 G=2 T=3, first base in the most significant bits;
@@ -383,6 +385,63 @@ uint64_t oracle_supermers(const char* reads, const uint64_t* offsets, uint64_t n
         }
     }
     return ns;
+}
+
+// Extension information (Sec. 3.3.2): for every kept k-mer, the ID of each
+// read it occurs in and its position in that read.  Written out as its
+// definition: every valid window yields (canonical key, read, position);
+// the triples are sorted, so the occurrences of one k-mer are adjacent and in
+// (read, position) order; each run whose length lies in [lo, hi] is kept.
+// Outputs (caller-allocated, sized by a first call with out arrays NULL that
+// returns the counts): *n_pairs kept k-mers with their counts as in
+// oracle_count, occ_read/occ_pos the kept k-mers' occurrences k-mer after
+// k-mer (the count of a k-mer is the length of its list).  Returns the
+// number of occurrences of kept k-mers, or -1 on bad arguments.
+int64_t oracle_count_ext(const char* reads, const uint64_t* offsets, uint64_t n_reads, int k, uint32_t lo,
+                         uint32_t hi, uint64_t* n_pairs, uint64_t* kmers_out, uint32_t* counts_out,
+                         uint32_t* occ_read, uint32_t* occ_pos) {
+    if (k < 1 || k > 64 || lo > hi || !n_pairs) return -1;
+    struct occ {
+        u128 key;
+        uint64_t read, pos;
+    };
+    std::vector<occ> all;
+    all.reserve(oracle_n_windows(reads, offsets, n_reads, k));
+    for (uint64_t r = 0; r < n_reads; ++r) {
+        const char* s = reads + offsets[r];
+        uint64_t len = offsets[r + 1] - offsets[r];
+        for (uint64_t i = 0; i + (uint64_t)k <= len; ++i)
+            if (all_acgt(s + i, k)) all.push_back({canonical_code(s + i, k), r, i});
+    }
+    std::sort(all.begin(), all.end(), [](const occ& a, const occ& b) {
+        if (a.key != b.key) return a.key < b.key;
+        if (a.read != b.read) return a.read < b.read;
+        return a.pos < b.pos;
+    });
+    const int kw = k <= 32 ? 1 : 2;
+    uint64_t np = 0, no = 0;
+    size_t i = 0;
+    while (i < all.size()) {
+        size_t j = i;
+        while (j < all.size() && all[j].key == all[i].key) ++j;
+        const uint64_t c = j - i;
+        if (c >= lo && c <= hi) {
+            if (kmers_out) {
+                kmers_out[np * kw] = (uint64_t)all[i].key;
+                if (kw == 2) kmers_out[np * kw + 1] = (uint64_t)(all[i].key >> 64);
+                counts_out[np] = (uint32_t)c;
+                for (size_t q = i; q < j; ++q) {
+                    occ_read[no + (q - i)] = (uint32_t)all[q].read;
+                    occ_pos[no + (q - i)] = (uint32_t)all[q].pos;
+                }
+            }
+            ++np;
+            no += c;
+        }
+        i = j;
+    }
+    *n_pairs = np;
+    return (int64_t)no;
 }
 
 // Stage reference for the sort alone: std::sort (Sec. 3.1).

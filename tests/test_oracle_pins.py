@@ -358,3 +358,43 @@ def test_n_windows_matches_closed_form(k):
     # windows never cross a read boundary: one read holding all bytes has more
     one = np.array([0, r.size], np.uint64)
     assert oracle.n_windows(r, one, k) == closed_form([b"".join(blobs)])
+
+
+# --- extension information (Sec. 3.3.2) -----------------------------------------
+
+def test_count_ext_golden_hand_examples():
+    cases = json.load(open(os.path.join(GOLDEN, "ext_example.json")))["cases"]
+    for c in cases:
+        reads, offs = pack(c["reads"])
+        r = oracle.count_ext(reads, offs, c["k"], c["lo"], c["hi"])
+        assert r.kmers.tolist() == c["kmers"], c["name"]
+        assert r.counts.tolist() == c["counts"], c["name"]
+        occ = [[[int(r.occ_read[j]), int(r.occ_pos[j])] for j in range(int(r.occ_offsets[i]), int(r.occ_offsets[i + 1]))]
+               for i in range(len(r.counts))]
+        assert occ == c["occurrences"], c["name"]
+
+
+@pytest.mark.parametrize("k", [3, 8, 21, 31, 33, 64])
+def test_count_ext_matches_string_brute_force(k):
+    reads, offs = datagen.random_reads(500 + k, 120, 0, 90, p_invalid=0.02, invalid=b"Nn")
+    strs = strs_of(reads, offs) + ["AC" * 40, "A" * 70, "AC" * 40]
+    reads, offs = pack(strs)
+    where = defaultdict(list)
+    for ri, s in enumerate(strs):
+        for i in range(len(s) - k + 1):
+            w = s[i:i + k]
+            if all(ch in "ACGT" for ch in w):
+                where[to_int(canonical_str(w))].append((ri, i))
+    lo, hi = 2, 50
+    want = sorted((key, occ) for key, occ in where.items() if lo <= len(occ) <= hi)
+    r = oracle.count_ext(reads, offs, k, lo, hi)
+    got = []
+    for i in range(len(r.counts)):
+        key = key_int(r, i)
+        occ = [(int(r.occ_read[j]), int(r.occ_pos[j])) for j in range(int(r.occ_offsets[i]), int(r.occ_offsets[i + 1]))]
+        assert len(occ) == int(r.counts[i])
+        got.append((key, occ))
+    assert got == want
+    # the same kept k-mers and counts as the plain count
+    plain = oracle.count(reads, offs, k, lo, hi)
+    assert np.array_equal(plain.kmers, r.kmers) and np.array_equal(plain.counts, r.counts)
