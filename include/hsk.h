@@ -135,6 +135,26 @@ int hsk_count_device(hsk_ctx* ctx, const char* d_reads, const uint64_t* d_offset
                      uint64_t n_reads, uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi,
                      void* stream, hsk_result* out);
 
+/* Counting with extension information (Sec. 3.3.2: the ID of the read a
+ * k-mer was extracted from and its position in that read, which seed-and-
+ * extend pipelines such as long-read overlap detection need).  counts is
+ * exactly what hsk_count returns.  Each kept k-mer i (in the ascending order
+ * of counts.kmers) has counts.counts[i] occurrences, listed at
+ * [occ_offsets[i], occ_offsets[i+1]) of occ_read (0-based read index) and
+ * occ_pos (0-based start of the window in that read), in ascending (read,
+ * position) order.  All arrays are host memory owned by the context, valid
+ * until its next counting call.  Errors as hsk_count, and HSK_EOVERFLOW for
+ * 2^32 reads or more, or a read of 2^32 bases or more. */
+typedef struct {
+    hsk_result counts;
+    uint64_t n_occ;               /* occurrences of the kept k-mers (the sum of their counts) */
+    const uint64_t* occ_offsets;  /* counts.n_pairs + 1 entries */
+    const uint32_t* occ_read;     /* n_occ read indices */
+    const uint32_t* occ_pos;      /* n_occ positions in the read */
+} hsk_ext_result;
+int hsk_count_ext(hsk_ctx* ctx, const char* reads, const uint64_t* offsets, uint64_t n_reads, int k, int m,
+                  uint32_t lo, uint32_t hi, hsk_ext_result* out);
+
 /* Copy the arrays of a result (as returned by any counting call on this
  * context) into caller memory: kmers_dst n_pairs * key_words words,
  * counts_dst n_pairs words, hist_dst hist_len words; any destination may be

@@ -92,6 +92,24 @@ int hsk_stage_rle(hsk_ctx* ctx, const uint64_t* d_sorted, uint64_t n, int key_wo
 int hsk_stage_order(hsk_ctx* ctx, uint64_t* d_keys, uint32_t* d_counts, uint64_t n,
                     int key_words, int key_bits, void* stream);
 
+/* The paper's compact encoding of extension information (Sec. 3.3.2: an
+ * item whose read ID and position both differ from the previous item's by
+ * a value that fits an int8 is sent as the two differences, else in full;
+ * a flag byte per item says which).  The stream of n items (d_read[i],
+ * d_pos[i]) becomes bytes at d_out (out_cap >= 9 n): per item a flag byte
+ * (1 = deltas, 0 = full), then either two int8 differences from the previous
+ * item, or the uint32 read and uint32 position, little endian.  Items are
+ * cut into chunks of HSK_EXT_CHUNK; a chunk's first item is always full and
+ * d_chunk_off[c] (ceil(n / HSK_EXT_CHUNK) entries, written) is its byte
+ * offset, so chunks decode independently.  *n_bytes receives the stream's
+ * length.  hsk_stage_ext_decode is the inverse; HSK_EINVAL for a malformed
+ * stream.  Device pointers; ordered on `stream`, complete on return. */
+#define HSK_EXT_CHUNK 1024
+int hsk_stage_ext_encode(hsk_ctx* ctx, const uint32_t* d_read, const uint32_t* d_pos, uint64_t n, uint8_t* d_out,
+                         uint64_t out_cap, uint64_t* d_chunk_off, uint64_t* n_bytes, void* stream);
+int hsk_stage_ext_decode(hsk_ctx* ctx, const uint8_t* d_in, uint64_t n_bytes, const uint64_t* d_chunk_off, uint64_t n,
+                         uint32_t* d_read, uint32_t* d_pos, void* stream);
+
 /* Stage S4's key sort for callers that cannot allocate device memory (the
  * paper has no counterpart: this serves callers of this library, not the
  * method).  Such callers are, for example, processes whose device memory is

@@ -57,6 +57,11 @@ class _Result(C.Structure):
                 ("n_chunks", C.c_uint32), ("n_supermers", C.c_uint64), ("device_ms", C.c_double)]
 
 
+class _ExtResult(C.Structure):
+    _fields_ = [("counts", _Result), ("n_occ", C.c_uint64), ("occ_offsets", C.c_void_p), ("occ_read", C.c_void_p),
+                ("occ_pos", C.c_void_p)]
+
+
 class _Job(C.Structure):
     _fields_ = [("reads", C.c_void_p), ("offsets", C.c_void_p), ("n_reads", C.c_uint64),
                 ("k", C.c_int), ("m", C.c_int), ("lo", C.c_uint32), ("hi", C.c_uint32)]
@@ -87,6 +92,9 @@ def load():
             "hsk_autotune": ([P, C.POINTER(_Job), u32, i32, C.POINTER(_TuneResult)], i32),
             "hsk_tune_current": ([P, C.POINTER(_TuneResult)], i32),
             "hsk_host_pin": ([P, u64], i32),
+            "hsk_count_ext": ([P, P, P, u64, i32, i32, u32, u32, C.POINTER(_ExtResult)], i32),
+            "hsk_stage_ext_encode": ([P, P, P, u64, P, u64, P, C.POINTER(u64), P], i32),
+            "hsk_stage_ext_decode": ([P, P, u64, P, u64, P, P, P], i32),
             "hsk_host_unpin": ([P], i32),
             "hsk_tune_set": ([P, C.POINTER(_TuneResult)], i32),
             "hsk_submit": ([P, C.POINTER(_Job), C.POINTER(u64)], i32),
@@ -148,6 +156,7 @@ def _stream_ptr(stream):
 
 
 NOALLOC_MAX_KEYS = {1: 1 << 20, 2: 1 << 19}
+EXT_CHUNK = 1024  # items per independently decodable chunk of the extension codec (HSK_EXT_CHUNK)
 
 
 def pinned_empty(nbytes: int) -> np.ndarray:
@@ -270,6 +279,34 @@ class Context:
         self._check(self.lib.hsk_count(self.h, _ptr(reads), _ptr(offsets), offsets.size - 1, k, m,
                                        lo, hi, C.byref(r)))
         return _host_result(r, copy)
+
+    def count_ext(self, reads, offsets, k: int, m: int, lo: int, hi: int):
+        """hsk_count_ext: (CountResult, occ_offsets, occ_read, occ_pos) as numpy copies."""
+        reads, offsets = _u8(reads), _u64(offsets)
+        r = _ExtResult()
+        self._check(self.lib.hsk_count_ext(self.h, _ptr(reads), _ptr(offsets), offsets.size - 1, k, m, lo, hi,
+                                           C.byref(r)))
+        res = _host_result(r.counts, True)
+        np_, no = int(r.counts.n_pairs), int(r.n_occ)
+        off = np.ctypeslib.as_array(C.cast(r.occ_offsets, C.POINTER(C.c_uint64)), shape=(np_ + 1,)).copy()
+        if no:
+            rd = np.ctypeslib.as_array(C.cast(r.occ_read, C.POINTER(C.c_uint32)), shape=(no,)).copy()
+            ps = np.ctypeslib.as_array(C.cast(r.occ_pos, C.POINTER(C.c_uint32)), shape=(no,)).copy()
+        else:
+            rd, ps = np.zeros(0, np.uint32), np.zeros(0, np.uint32)
+        return res, off, rd, ps
+
+    def stage_ext_encode(self, read_t, pos_t, out_t, chunk_off_t, stream=None) -> int:
+        """Encode n = read_t.numel() items; returns the byte length."""
+        nb = C.c_uint64()
+        self._check(self.lib.hsk_stage_ext_encode(self.h, _tptr(read_t), _tptr(pos_t), int(read_t.numel()),
+                                                  _tptr(out_t), int(out_t.numel()), _tptr(chunk_off_t),
+                                                  C.byref(nb), _stream_ptr(stream)))
+        return nb.value
+
+    def stage_ext_decode(self, in_t, n_bytes: int, chunk_off_t, n: int, read_t, pos_t, stream=None):
+        self._check(self.lib.hsk_stage_ext_decode(self.h, _tptr(in_t), n_bytes, _tptr(chunk_off_t), n,
+                                                  _tptr(read_t), _tptr(pos_t), _stream_ptr(stream)))
 
     def count_device(self, reads_t, offsets_t, k: int, m: int, lo: int, hi: int, stream=None,
                      n_bases: int | None = None) -> _Result:

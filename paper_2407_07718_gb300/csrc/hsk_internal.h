@@ -176,4 +176,20 @@ void launch_rle_write(const void* keys, uint64_t n, int key_words, const uint32_
                       const uint64_t* out_off, uint32_t lo, uint32_t hi, void* out_keys, uint32_t* out_counts,
                       uint64_t out_cap, int* err, int grid, cudaStream_t st);
 
+// ---- extension information (k_ext.cu) ---------------------------------------
+void launch_ext_insert(const void* keys, int key_words, uint64_t n, uint32_t* table, uint32_t mask, int* err,
+                       cudaStream_t st);
+void launch_ext_scan(const uint64_t* packed, const uint64_t* invalid, const uint64_t* start, uint64_t n_bases, int k,
+                     const void* kept, const uint32_t* table, uint32_t mask, bool wide_out, void* out,
+                     uint64_t out_cap, uint64_t* cursor, int* err, int grid, cudaStream_t st);
+void launch_ext_decode_pos(const void* comp, bool wide, uint64_t n, const uint64_t* offsets, uint64_t n_reads,
+                           uint32_t* occ_read, uint32_t* occ_pos, int grid, cudaStream_t st);
+uint64_t ext_chunk_items();
+void launch_ext_sizes(const uint32_t* rd, const uint32_t* ps, uint64_t n, uint32_t* size, int grid, cudaStream_t st);
+void launch_ext_encode(const uint32_t* rd, const uint32_t* ps, uint64_t n, const uint64_t* off, uint8_t* out,
+                       int grid, cudaStream_t st);
+void launch_ext_chunk_off(const uint64_t* off, uint64_t n, uint64_t* chunk_off, int grid, cudaStream_t st);
+void launch_ext_decode(const uint8_t* in, uint64_t n_bytes, uint64_t n, const uint64_t* chunk_off, uint32_t* rd,
+                       uint32_t* ps, int* err, int grid, cudaStream_t st);
+
 }  // namespace hsk

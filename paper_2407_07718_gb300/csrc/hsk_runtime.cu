@@ -590,7 +590,7 @@ static int sort_segments(hsk_ctx* c, void* a, void* b, uint32_t* va, uint32_t* v
 }
 
 // A plain (one-segment) sort of n keys (with optional values) in place.
-static int plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int key_words, int key_bits,
+int hsk_plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int key_words, int key_bits,
                       DevBuf& alt_keys, DevBuf* alt_vals, cudaStream_t st) {
     if (n <= 1) return HSK_OK;
     size_t kb = (size_t)key_words * 8;
@@ -671,12 +671,12 @@ int hsk_order_pairs(hsk_ctx* c, void* keys, uint32_t* counts, uint64_t n, int ke
     const int spare = 64 * key_words - cshift;
     if (n > 1 && count_max > 0 && spare > 0 && spare < 64 && (uint64_t)count_max < (1ULL << spare)) {
         launch_pack_pairs(keys, counts, n, key_words, cshift, false, c->num_sms * 8, st);
-        TRY(plain_sort(c, keys, nullptr, n, key_words, key_bits, c->pair_alt_keys, nullptr, st));
+        TRY(hsk_plain_sort(c, keys, nullptr, n, key_words, key_bits, c->pair_alt_keys, nullptr, st));
         launch_pack_pairs(keys, counts, n, key_words, cshift, true, c->num_sms * 8, st);
         CK(cudaGetLastError());
         return HSK_OK;
     }
-    return plain_sort(c, keys, counts, n, key_words, key_bits, c->pair_alt_keys, &c->pair_alt_counts, st);
+    return hsk_plain_sort(c, keys, counts, n, key_words, key_bits, c->pair_alt_keys, &c->pair_alt_counts, st);
 }
 
 // Split buckets [b0, b1) into at most C_want groups of roughly equal k-mer
@@ -878,7 +878,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
         launch_ov_gather(sub_off, left, n_ov, (uint64_t*)c->batch_c.p, kw, c->keys.p, c->batch_a.p, ov_keys,
                          c->d_err, c->num_sms * 4, st);
         CK(cudaGetLastError());
-        TRY(plain_sort(c, c->batch_a.p, nullptr, ov_keys, kw, key_bits, c->batch_b, nullptr, st));
+        TRY(hsk_plain_sort(c, c->batch_a.p, nullptr, ov_keys, kw, key_bits, c->batch_b, nullptr, st));
         TRY(hsk_rle_chunk(c, c->batch_a.p, ov_keys, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
     }
     c->last_ov_keys += ov_keys;
@@ -1243,7 +1243,7 @@ extern "C" int hsk_stage_sort(hsk_ctx* c, uint64_t* d_keys, uint64_t n, int key_
         CK(cudaMemsetAsync(c->counters, 0, HSK_N_COUNTERS * sizeof(uint32_t), st));
         c->ctr_used = 0;
         if (n <= 1) return HSK_OK;
-        TRY(plain_sort(c, d_keys, nullptr, n, key_words, key_bits, c->alt, nullptr, st));
+        TRY(hsk_plain_sort(c, d_keys, nullptr, n, key_words, key_bits, c->alt, nullptr, st));
         return hsk_read_device_error(c, st);
     });
 }

@@ -285,6 +285,7 @@ struct hsk_ctx {
     DevBuf loc_tab;                                                // on-chip path: sub-segment tables
     DevBuf batch_a, batch_b, batch_c, batch_d;                     // on-chip path: overflow keys, tile map
     DevBuf pack_tab, pack_stat;                                    // packed sets: set tables, per-set statistics
+    DevBuf ext_tab, ext_occ;                                       // extension information: key table, occurrence arrays
 
     // tuned parameters (0 = built-in default); see hsk_tune.cu
     struct Tune {
@@ -304,6 +305,8 @@ struct hsk_ctx {
 
     HostPool result_pool;                // host blocks of batched and served results (outlives them)
     HostResult host_res;                 // result of the last hsk_count
+    HostArr<uint64_t> ext_off;           // occurrence lists of the last hsk_count_ext
+    HostArr<uint32_t> ext_read, ext_pos;
     std::vector<HostResult> batch_res;   // results of the last hsk_count_batch
 
     ServeState* serve = nullptr;
@@ -325,7 +328,7 @@ struct hsk_ctx {
         return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
                 &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads, &rle_tiles,
                 &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &loc_tab, &batch_a,
-                &batch_b, &batch_c, &batch_d, &pack_tab, &pack_stat};
+                &batch_b, &batch_c, &batch_d, &pack_tab, &pack_stat, &ext_tab, &ext_occ};
     }
 };
 
@@ -398,6 +401,8 @@ int hsk_plan_chunks(hsk_ctx* c, const Supermers& S, int key_words, std::vector<s
 int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S, cudaStream_t st,
                   InputPipe* pipe, const SetMap* sets = nullptr);
 uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k);
+int hsk_plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int key_words, int key_bits, DevBuf& alt_keys,
+                   DevBuf* alt_vals, cudaStream_t st);
 int hsk_local_overflow(hsk_ctx* c, const uint64_t* sub_off, uint32_t n_ov1, uint32_t* ov_list, uint32_t* ov_list2,
                        uint32_t* ov_list3, int kw, int shift0, void* keys, uint32_t* kcount, uint32_t* kcv,
                        uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t H, uint32_t* d_max, uint64_t* d_distinct,
