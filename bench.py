@@ -432,11 +432,49 @@ def bench_second_workload(hsk, local: int, name: str, steps: int, warmup: int) -
     return out
 
 
+def bench_extension(hsk, local: int, rs, pin_reads, pin_offs, steps: int = 2) -> dict:
+    """Counting with extension information (Sec. 3.3.2) through hsk_count_ext
+    on the workload's pinned host inputs, against hsk_count, and the byte cost
+    of the extension payload: 8 bytes per occurrence (uint32 read + uint32
+    position) against the paper's encoding (flag byte + two int8 differences,
+    or the flag byte + the full pair) of the occurrences in read order, i.e.
+    the consecutive kept k-mers of each read."""
+    import torch
+    with hsk.Context(device=local) as ctx:
+        ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi, copy=False)
+        ctx.count_ext(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi, copy=False)
+        count_s = (time.perf_counter() - t0) / steps
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            res, off, rd, ps = ctx.count_ext(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi)
+        ext_s = (time.perf_counter() - t0) / steps
+        n_occ = int(rd.size)
+        order = np.lexsort((ps, rd))
+        d_rd = torch.from_numpy(rd[order].view(np.int32)).cuda(local)
+        d_ps = torch.from_numpy(ps[order].view(np.int32)).cuda(local)
+        out = torch.empty(max(9 * n_occ, 1), dtype=torch.uint8, device=f"cuda:{local}")
+        chunks = max((n_occ + hsk.EXT_CHUNK - 1) // hsk.EXT_CHUNK, 1)
+        coff = torch.empty(chunks, dtype=torch.int64, device=f"cuda:{local}")
+        nb = ctx.stage_ext_encode(d_rd, d_ps, out, coff)
+        del out, d_rd, d_ps, coff
+    torch.cuda.empty_cache()
+    enc = nb + 8 * chunks
+    return {"count_ms": count_s * 1e3, "count_ext_ms": ext_s * 1e3, "n_pairs": int(res.counts.size),
+            "n_occ": n_occ, "payload_raw_bytes": 8 * n_occ, "payload_encoded_bytes": enc,
+            "encoded_over_raw": enc / max(1, 8 * n_occ),
+            "note": "hsk_count and hsk_count_ext from pinned host inputs, results copied back; encoded = "
+                    "the paper's extension encoding of the occurrences in read order, plus its chunk index"}
+
+
 def run_ablations(rs, local: int) -> dict:
     """Diagnostics of the bucketing on the workload's reads (device-resident):
     bucket balance (k-mers per bucket, from the S3 stage) at 256 and 4096
-    buckets, and a sweep of the minimizer length m with the whole count's
-    device time, the supermers formed and their mean k-mers."""
+    buckets, a sweep of the minimizer length m with the whole count's device
+    time, the supermers formed and their mean k-mers, and hash against
+    lexical minimizer order (S2's time, supermers, balance; same counts)."""
     import torch
     import paper_2407_07718_gb300 as hsk
     torch.cuda.set_device(local)
@@ -473,7 +511,40 @@ def run_ablations(rs, local: int) -> dict:
                           "n_supermers": int(r.n_supermers),
                           "kmers_per_supermer": int(r.n_windows) / max(1, int(r.n_supermers)),
                           "n_distinct": int(r.n_distinct), "n_pairs": int(r.n_pairs)})
-    return {"bucket_balance": balance, "m_sweep": sweep}
+        # E14: hash-ordered against lexically ordered minimizers (Sec. 3.2):
+        # the same counts, different supermers and bucket balance, S2's cost
+        order = []
+        for lexical in (False, True):
+            with hsk.Context(device=local, lexical_minimizers=lexical) as c2:
+                B = 4096
+                bk = torch.zeros(B, dtype=torch.int64, device=dev)
+                br = torch.zeros(B + 1, dtype=torch.int64, device=dev)
+                c2.stage_supermers(d_reads, d_offs, rs.k, rs.m, B, bk, br, stream=stream)
+                torch.cuda.synchronize()
+                v = bk.cpu().numpy().astype(np.float64)
+                for _ in range(2):
+                    r = c2.count_device(d_reads, d_offs, rs.k, rs.m, rs.lo, rs.hi, stream=stream)
+                c2.profile(True)
+                c2.profile_read(reset=True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 3
+                e0.record(stream)
+                for _ in range(reps):
+                    r = c2.count_device(d_reads, d_offs, rs.k, rs.m, rs.lo, rs.hi, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                st_ms, _ = c2.profile_read(reset=True)
+                order.append({"order": "lexical" if lexical else "hash", "m": rs.m,
+                              "ms_per_count": e0.elapsed_time(e1) / reps,
+                              "s2_ms": st_ms[1] / reps, "stages_ms": [x / reps for x in st_ms],
+                              "n_supermers": int(r.n_supermers),
+                              "kmers_per_supermer": int(r.n_windows) / max(1, int(r.n_supermers)),
+                              "buckets_4096_max_over_mean": float(v.max() / v.mean()),
+                              "buckets_4096_cv": float(v.std() / v.mean()),
+                              "n_distinct": int(r.n_distinct), "n_pairs": int(r.n_pairs),
+                              "keys_off_chip": c2.last_overflow()})
+        assert order[0]["n_distinct"] == order[1]["n_distinct"] and order[0]["n_pairs"] == order[1]["n_pairs"]
+    return {"bucket_balance": balance, "m_sweep": sweep, "minimizer_order": order}
 
 
 def dist_setup():
@@ -520,6 +591,7 @@ def main():
                     help="windows in the oracle's bounded sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-ext", action="store_true", help="skip the extension-information leg")
     ap.add_argument("--second-workload", default="short_read", choices=["short_read", "long_read", "none"],
                     help="a second plain workload reported under its own key (default: short-read, k=55)")
     ap.add_argument("--second-steps", type=int, default=5)
@@ -686,6 +758,11 @@ def main():
            "ms_per_step": dt * 1e3}
     assert r.n_windows == n_windows
 
+    ext_leg = None
+    if rank == 0 and world == 1 and not args.no_ext:
+        ext_leg = bench_extension(hsk, local, rs, pin_reads, pin_offs)
+        print(json.dumps({"extension": ext_leg}), file=sys.stderr, flush=True)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         nw, times, nreads = run_cpu_oracle(rs, args.cpu_windows)
@@ -722,6 +799,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "stages_ms_per_step": {n: v / args.steps for n, v in zip(hsk.Context.STAGES, stage_ms)}}
+        if ext_leg is not None:
+            line["extension"] = ext_leg
         line.update(forms)
         print(json.dumps(line))
     if pg is not None:

@@ -68,6 +68,11 @@ typedef struct {
                               the same either way. */
     const char* tune_cache; /* file of tuned parameters: read at hsk_create,
                                appended to by hsk_autotune; NULL = none */
+    int minimizer_order;    /* 0 (default) = m-mers ordered by a hash of the
+                               canonical m-mer (Sec. 3.2); 1 = lexically, by the
+                               canonical m-mer's code (its top 32 bits for
+                               m > 16).  Counts are the same either way; only
+                               supermers, buckets and speed change. */
 } hsk_config;
 
 /* A counting result.  All arrays are owned by the context and stay valid until

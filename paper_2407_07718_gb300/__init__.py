@@ -41,7 +41,7 @@ class _Config(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_uint64), ("hist_len", C.c_uint32),
                 ("n_buckets", C.c_uint32), ("radix_bits", C.c_uint32),
                 ("max_chunk_kmers", C.c_uint32), ("seed", C.c_uint64), ("autotune", C.c_int),
-                ("local_sort", C.c_int), ("tune_cache", C.c_char_p)]
+                ("local_sort", C.c_int), ("tune_cache", C.c_char_p), ("minimizer_order", C.c_int)]
 
 
 class _TuneResult(C.Structure):
@@ -233,7 +233,7 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, hist_len: int = 65536, n_buckets: int = 0,
                  max_chunk_kmers: int = 0, seed: int = DEFAULT_SEED, autotune: bool = True,
-                 local_sort: bool = True, tune_cache: str | None = None):
+                 local_sort: bool = True, tune_cache: str | None = None, lexical_minimizers: bool = False):
         self.lib = load()
         cfg = _Config()
         self.lib.hsk_config_default(C.byref(cfg))
@@ -241,6 +241,7 @@ class Context:
         cfg.n_buckets, cfg.max_chunk_kmers, cfg.seed, cfg.autotune = n_buckets, max_chunk_kmers, seed, int(autotune)
         cfg.local_sort = int(local_sort)
         cfg.tune_cache = tune_cache.encode() if tune_cache else None
+        cfg.minimizer_order = 1 if lexical_minimizers else 0
         h = C.c_void_p()
         rc = self.lib.hsk_create(C.byref(h), C.byref(cfg))
         if rc != HSK_OK:

@@ -47,6 +47,7 @@ struct SmParams {
     uint64_t n_packed_words, n_mask_words;
     int k, m, w;
     uint32_t seed32;
+    int lexical;              // 1: m-mers ordered by their code (lexical), 0: by hash
     uint32_t n_buckets;       // a power of two (one set), or the buckets of all packed sets
     int nmax;                 // k-mers per supermer record at most
     uint32_t nmax_magic;      // ceil(2^32 / nmax): q = umulhi(x, magic) = x / nmax for x < 2^24

@@ -152,7 +152,9 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
         hsk_config cfg;
         if (cfg_in) cfg = *cfg_in;
         else hsk_config_default(&cfg);
-        if (cfg.hist_len < 2 || (cfg.radix_bits != 0 && cfg.radix_bits != 8)) return HSK_EINVAL;
+        if (cfg.hist_len < 2 || (cfg.radix_bits != 0 && cfg.radix_bits != 8) || cfg.minimizer_order < 0 ||
+            cfg.minimizer_order > 1)
+            return HSK_EINVAL;
         if (cfg.n_buckets && (cfg.n_buckets > HSK_MAX_BUCKETS || (cfg.n_buckets & (cfg.n_buckets - 1))))
             return HSK_EINVAL;  // a power of two: the bucket is a mask of the hash
         hsk_ctx* c = new hsk_ctx();
@@ -399,6 +401,7 @@ static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t 
     P.m = m;
     P.w = k - m + 1;
     P.seed32 = (uint32_t)c->cfg.seed;
+    P.lexical = c->cfg.minimizer_order == 1;
     P.n_buckets = B;
     P.rec_words = k <= 32 ? 2 : 4;
     P.nmax = (P.rec_words * 32 - 4) - k + 1;  // bases per record minus (k - 1)

@@ -56,12 +56,20 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     return h;
 }
 
-// Score of the m-mer at local base q of the staged words.
+// Score of the m-mer at local base q of the staged words.  Hash order (the
+// paper's choice, Sec. 3.2): MurmurHash3's finalizer of the canonical m-mer.
+// Lexical order (the alternative the paper compares against): the canonical
+// m-mer's code itself -- its top 32 bits when m > 16, so that the score stays
+// 32-bit (m-mers sharing their first 16 bases then tie, which only groups them
+// in one bucket).  Either way the score is a function of the canonical m-mer,
+// so a k-mer and its reverse complement share their minimizer and bucket.
+template <bool LEX>
 __device__ __forceinline__ uint32_t mmer_score(const u64* pk, int q, int m, uint32_t seed) {
     u64 f = extract_k64(pk, (u64)q, m);
     u64 r = revcomp64(f, m);
     u64 c = f < r ? f : r;
-    return fmix32((uint32_t)c ^ (uint32_t)(c >> 32) ^ seed);
+    if constexpr (LEX) return m > 16 ? (uint32_t)(c >> (2 * m - 32)) : (uint32_t)c;
+    else return fmix32((uint32_t)c ^ (uint32_t)(c >> 32) ^ seed);
 }
 
 // Value at index lane + d (0 <= d < 32) of the 32*NREG-long sequence held as
@@ -126,7 +134,7 @@ __device__ __forceinline__ u64 make_desc(u64 pos, uint32_t n, uint32_t b) {
     return pos | ((u64)n << 40) | ((u64)b << 48);
 }
 
-template <int MODE, bool WIDE, int NREG>
+template <int MODE, bool WIDE, int NREG, bool LEX>
 __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     u64* s_pk = reinterpret_cast<u64*>(smem);
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
         // rolling m-mer scores: X[r] = score at local base 32*(s + r) + lane
         uint32_t X[NREG];
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) X[r] = mmer_score(wpk, 32 * r + lane, m, P.seed32);
+        for (int r = 0; r < NREG; ++r) X[r] = mmer_score<LEX>(wpk, 32 * r + lane, m, P.seed32);
 
         int c_valid = 0, c_runstart = -1;   // carry from lane 31 of the previous step
         uint32_t c_b = 0;
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
             // roll the scores forward by one step
 #pragma unroll
             for (int r = 0; r + 1 < NREG; ++r) X[r] = X[r + 1];
-            X[NREG - 1] = mmer_score(wpk, 32 * (s + NREG) + lane, m, P.seed32);
+            X[NREG - 1] = mmer_score<LEX>(wpk, 32 * (s + NREG) + lane, m, P.seed32);
         }
         if (MODE != SM_DUMP) {  // the tile edge ends every open supermer
             const int nv = lane < 31 ? (int)((pvmask >> (lane + 1)) & 1u) : 0;
@@ -339,7 +347,7 @@ static void launch_mode(const SmParams& p, cudaStream_t st) {
     count_launch();
 #define HSK_SM_LAUNCH(W, NR)                                                                 \
     do {                                                                                     \
-        auto fn = k_supermer<MODE, W, NR>;                                                   \
+        auto fn = p.lexical ? k_supermer<MODE, W, NR, true> : k_supermer<MODE, W, NR, false>; \
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
         fn<<<grid, 256, sm, st>>>(p);                                                        \
     } while (0)
@@ -359,8 +367,10 @@ void launch_supermer(int mode, const SmParams& p, cudaStream_t st) {
 int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets) {
     size_t sm = supermer_smem_bytes(mode, n_buckets);
     int n = 0;
-    const void* fn = wide ? (nreg == 2 ? (const void*)k_supermer<SM_DESC, true, 2> : (const void*)k_supermer<SM_DESC, true, 3>)
-                          : (nreg == 2 ? (const void*)k_supermer<SM_DESC, false, 2> : (const void*)k_supermer<SM_DESC, false, 3>);
+    const void* fn = wide ? (nreg == 2 ? (const void*)k_supermer<SM_DESC, true, 2, false>
+                                       : (const void*)k_supermer<SM_DESC, true, 3, false>)
+                          : (nreg == 2 ? (const void*)k_supermer<SM_DESC, false, 2, false>
+                                       : (const void*)k_supermer<SM_DESC, false, 3, false>);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, sm) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;

@@ -250,3 +250,20 @@ def test_task_with_too_many_distinct_keys_takes_the_global_path(hsk):
         got = ctx.count(reads, offs, 31, 17, 2, 1000)
         assert ctx.last_overflow() == 40_000
     assert_same_result(got, want, "distinct-heavy")
+
+
+@pytest.mark.parametrize("k,m,B", [(31, 17, 0), (55, 21, 0), (21, 11, 64), (31, 11, 1)])
+def test_lexical_minimizer_order_gives_the_same_counts(hsk, tiny, k, m, B):
+    """E14: ordering m-mers lexically instead of by hash changes supermers and
+    buckets (poly-A-like m-mers attract many k-mers) but not one count."""
+    n = 6000
+    reads, offs = tiny.reads[: int(tiny.offsets[n])], tiny.offsets[: n + 1]
+    reads = np.concatenate([reads, np.frombuffer(b"A" * 3000 + b"C" * 500, np.uint8)])
+    offs = np.concatenate([offs, [offs[-1] + 3000, offs[-1] + 3500]]).astype(np.uint64)
+    want = oracle.count(reads, offs, k, 2, 1000)
+    with hsk.Context(lexical_minimizers=True, n_buckets=B) as lex, hsk.Context(n_buckets=B) as hsh:
+        a = lex.count(reads, offs, k, m, 2, 1000)
+        b = hsh.count(reads, offs, k, m, 2, 1000)
+    assert_same_result(a, want, f"lexical k={k}")
+    assert_same_result(b, want, f"hash k={k}")
+    assert a.n_supermers != b.n_supermers or B == 1

@@ -236,3 +236,46 @@ def test_s6_order_pairs(hsk, kw, bits):
     gk = host_u64(tk).reshape(keys.shape)
     gc = tc.cpu().numpy().view(np.uint32)
     assert np.array_equal(gk, keys[order]) and np.array_equal(gc, counts[order])
+
+
+def _lexical_minimum(strs_offs, k, m, pos):
+    """Per valid window start: the smallest lexical score (the canonical m-mer's
+    code, its top 32 bits when m > 16) over the window's k - m + 1 m-mers."""
+    reads, offs = strs_offs
+    b = reads.tobytes().decode()
+    code = {"A": 0, "C": 1, "G": 2, "T": 3}
+
+    def canon(s):
+        f = 0
+        for ch in s:
+            f = (f << 2) | code[ch]
+        r = 0
+        for ch in reversed(s):
+            r = (r << 2) | (3 - code[ch])
+        c = min(f, r)
+        return c >> (2 * m - 32) if m > 16 else c
+
+    return np.array([min(canon(b[p + j:p + j + m]) for j in range(k - m + 1)) for p in pos.tolist()], np.uint64)
+
+
+@pytest.mark.parametrize("k,m", [(21, 11), (31, 17), (55, 21), (16, 16)])
+def test_s2_windows_lexical_order(hsk, k, m):
+    """E14's alternative minimizer order (Sec. 3.2): with lexical order the
+    window minimum is the smallest canonical m-mer code, checked against a
+    brute force over the window's m-mers."""
+    import torch
+    reads, offs = _inputs(k * 10 + m, n_reads=40, lo=0, hi=400, extra=["ACGT" * 20, "G" * 90])
+    n = reads.size
+    pos, key, _, _ = oracle.windows(reads, offs, k, m)
+    with hsk.Context(lexical_minimizers=True) as ctx:
+        valid = empty_dev(n, torch.uint8)
+        keys = empty_dev(2 * n, torch.int64)
+        mins = empty_dev(n, torch.int64)
+        ctx.stage_windows(dev(reads), dev_u64(offs), k, m, valid, keys, mins)
+        valid = valid.cpu().numpy()[:n]
+        keys = host_u64(keys)[: 2 * n].reshape(n, 2)
+        mins = host_u64(mins)[:n]
+    gv = np.nonzero(valid)[0]
+    assert np.array_equal(gv.astype(np.uint64), pos)
+    assert np.array_equal(keys[gv], key)
+    assert np.array_equal(mins[gv], _lexical_minimum((reads, offs), k, m, pos))
