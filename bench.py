@@ -48,11 +48,14 @@ UNIT = "k-mers/s"
 # at capture time; used only while that source is unchanged.
 #   inst  : warp instructions issued per key (both on-chip passes)
 #   dram  : DRAM bytes read + written per key (both passes)
+#   smem_wavefronts : shared-memory wavefronts per key (both passes); an SM's
+#           shared-memory pipe processes at most one wavefront per cycle
 # The commands that produced them are in profiles/.
 NCU_PER_KEY = {
-    # long-read workload, k=31: k_local_sort passes 0 + 1, smsp__inst_executed.sum and DRAM
-    # bytes from the 0.1-scale case (149.6 M keys), per key
-    ("long_read", "28196a6506179be2"): {"inst": 11.384, "dram": 8.3418},
+    # long-read workload, k=31: k_local_sort passes 0 + 1 (the heavy-hitter kernel does not
+    # run at this scale), smsp__inst_executed.sum, DRAM bytes and shared-memory wavefronts
+    # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) from the 0.1-scale case (149.6 M keys)
+    ("long_read", "96602f4d3cddc5e1"): {"inst": 11.4753, "dram": 8.3887, "smem_wavefronts": 2.3459},
 }
 # Warp schedulers per SM (Blackwell): each issues at most one warp instruction
 # per cycle; the issue peak is SMs (queried from the device) x this x the SM
@@ -709,12 +712,19 @@ def main():
         achieved = inst / (launch_ms / 1e3) / 1e9 if inst and launch_ms > 0 else None
         hbm_bytes = n_windows * kb + int(res.n_pairs) * (kb + 4)
         hbm_achieved = hbm_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+        wav = cnt.get("smem_wavefronts") * n_windows if cnt else None
+        smem_peak = n_sms * clk_mhz / 1e3  # G wavefronts / s: one per SM per cycle
+        smem_achieved = wav / (launch_ms / 1e3) / 1e9 if wav and launch_ms > 0 else None
         roofline = {"bound": "alu", "kernel": "k_local_sort (sub-segment sort + count in shared memory, both passes)",
                     "achieved": achieved, "peak": peak_issue, "unit": "G warp-instructions/s",
                     "frac": achieved / peak_issue if achieved else None,
                     "traffic": cnt["dram"] * n_windows if cnt else None,
                     "peak_source": f"issue slots: {n_sms} SMs x {SCHEDULERS_PER_SM} schedulers x {clk_mhz:.0f} MHz (sampled)",
                     "inst_per_launch": inst, "launch_ms": launch_ms,
+                    "smem_view": {"wavefronts_per_launch": wav, "achieved": smem_achieved, "peak": smem_peak,
+                                  "unit": "G shared-memory wavefronts/s",
+                                  "frac": smem_achieved / smem_peak if smem_achieved else None,
+                                  "peak_source": f"{n_sms} SMs x 1 wavefront per cycle x {clk_mhz:.0f} MHz"},
                     "hbm_view": {"bytes_per_launch": hbm_bytes, "achieved": hbm_achieved, "unit": "GB/s",
                                  "frac": hbm_achieved / peaks["hbm_gbs"],
                                  "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs copy bandwidth)"}}
