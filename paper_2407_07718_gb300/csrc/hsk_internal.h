@@ -108,7 +108,7 @@ void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hi
 // Digit histograms of C consecutive segments of plain keys (keys
 // [key_base[c], key_base[c+1]) of n): hist[c][p][256], accumulated.
 void launch_digit_hist_seg(const void* keys, int key_words, const uint64_t* key_base, uint32_t C, uint64_t n,
-                           uint64_t* hist, int n_pass, cudaStream_t st);
+                           uint64_t* hist, int n_pass, cudaStream_t st, int shift0 = 0);
 // dst[i] = src[idx[i]] for i < n
 void launch_gather_u64(const uint64_t* src, const uint64_t* idx, uint32_t n, uint64_t* dst, cudaStream_t st);
 // doff[p][c][d] = key_base[c] + exclusive prefix over d of hist[c][p][d]
@@ -154,9 +154,19 @@ void launch_heavy_count(const uint64_t* sub_off, const uint32_t* list, uint32_t 
                         uint32_t* kcount, uint32_t* kc, uint32_t* ov_list, uint64_t* ov_stats, uint32_t lo,
                         uint32_t hi, uint64_t* hist, uint32_t hist_len, uint32_t* max_count, uint64_t* n_distinct,
                         const uint32_t* grp_set, uint32_t* claim, int* err, int num_sms, cudaStream_t st);
+// n_groups > 0: digit-major output (out_off indexed d * n_groups + g)
 void launch_compact(const uint64_t* sub_off, const uint32_t* kc, const uint64_t* out_off, uint32_t n_sub,
-                    int key_words, const void* keys, const uint32_t* kcount, void* out_keys, uint32_t* out_counts,
-                    uint64_t out_cap, int* err, int grid, cudaStream_t st);
+                    uint32_t n_groups, int key_words, const void* keys, const uint32_t* kcount, void* out_keys,
+                    uint32_t* out_counts, uint64_t out_cap, int* err, int grid, cudaStream_t st);
+void launch_transpose_kc(const uint32_t* kc, uint32_t n_groups, uint32_t* kc_t, int grid, cudaStream_t st);
+// S6 on chip: sub-range r holds pairs [bounds[r], bounds[r+1]) of (kin, vin)
+// that share their key bits from shift up; each is sorted by its key and
+// written to the same range of (kout, vout).  A sub-range over
+// range_sort_cap() sets *too_big and is skipped.
+uint32_t range_sort_cap(int key_words);
+void launch_range_sort(const void* kin, const uint32_t* vin, void* kout, uint32_t* vout, const uint64_t* bounds,
+                       uint32_t n_ranges, int key_words, int shift, int* too_big, uint32_t* claim, int num_sms,
+                       cudaStream_t st);
 void launch_ov_gather(const uint64_t* sub_off, const uint32_t* ov_list, uint32_t n_ov, uint64_t* ov_pre,
                       int key_words, const void* keys, void* dst, uint64_t dst_cap, int* err, int grid,
                       cudaStream_t st);

@@ -333,7 +333,7 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         const uint64_t kept = pair_off[S];
         Output O;
         TRY(hsk_grow_output(c, O, std::max<uint64_t>(kept, 1), kw, st));
-        launch_compact(sub_off, kcv, kc_off, (uint32_t)NS, kw, c->keys.p, (const uint32_t*)c->alt.p, c->out_keys.p,
+        launch_compact(sub_off, kcv, kc_off, (uint32_t)NS, 0, kw, c->keys.p, (const uint32_t*)c->alt.p, c->out_keys.p,
                        (uint32_t*)c->out_counts.p, kept, c->d_err, c->num_sms * 8, st);
         CK(cudaGetLastError());
     }

@@ -192,6 +192,7 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
         c->d_ndesc = (uint64_t*)(s + 32);
         c->d_nlocal = (uint64_t*)(s + 40);
         c->d_ovstats = (uint64_t*)(s + 48);
+        c->d_flag = (int*)(s + 112);
         c->counters = (uint32_t*)(s + 256);
         *out = c;
         return HSK_OK;
@@ -682,6 +683,69 @@ int hsk_order_pairs(hsk_ctx* c, void* keys, uint32_t* counts, uint64_t n, int ke
     return hsk_plain_sort(c, keys, counts, n, key_words, key_bits, c->pair_alt_keys, &c->pair_alt_counts, st);
 }
 
+// Stage S6 for kept pairs laid out by their top digit (c->s6_bounds holds
+// the 257 digit starts): one segmented LSD pass on the second digit groups
+// every top-digit range into 256 sub-ranges, then each of the 65,536
+// sub-ranges is sorted on chip (k_range_sort).  *done = false leaves the
+// pairs for the general path (keys of fewer than 24 bits, or a sub-range over
+// the on-chip capacity; the pairs are then back in place, unsorted).
+static int order_pairs_msd(hsk_ctx* c, uint64_t n, int kw, int key_bits, cudaStream_t st, bool* done) {
+    *done = false;
+    const int shift1 = key_bits - 16, shift2 = key_bits - 24;
+    if (shift2 < 0 || n < 2) return HSK_OK;
+    const size_t kb = (size_t)kw * 8;
+    const uint64_t* d_bounds = (const uint64_t*)c->s6_bounds.p;
+    std::vector<uint64_t> hb(257);
+    CK(cudaMemcpyAsync(hb.data(), d_bounds, 257 * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hb[256] != n) {
+        hsk_set_error(c, "S6: %llu pairs laid out by digit, %llu expected", (unsigned long long)hb[256],
+                      (unsigned long long)n);
+        return HSK_ECUDA;
+    }
+    const uint64_t TILE = onesweep_tile_keys(kw);
+    std::vector<uint32_t> ts(257);
+    uint64_t tiles = 0;
+    for (int d = 0; d < 256; ++d) {
+        ts[d] = (uint32_t)tiles;
+        tiles += (hb[d + 1] - hb[d] + TILE - 1) / TILE;
+    }
+    ts[256] = (uint32_t)tiles;
+    TRY(hsk_ensure(c, c->seg, 257 * 4, false));
+    CK(cudaMemcpyAsync(c->seg.p, ts.data(), 257 * 4, cudaMemcpyHostToDevice, st));
+    TRY(hsk_ensure(c, c->pass_hist, 256 * 256 * 8, false));
+    TRY(hsk_ensure(c, c->digit_off, (256 * 256 + 1) * 8, false));
+    TRY(hsk_ensure(c, c->pair_alt_keys, n * kb, false));
+    TRY(hsk_ensure(c, c->pair_alt_counts, n * 4, false));
+    TRY(hsk_ensure_status(c, tiles * 256 + 1, st));
+    uint64_t* doff = (uint64_t*)c->digit_off.p;
+    CK(cudaMemsetAsync(c->pass_hist.p, 0, 256 * 256 * 8, st));
+    launch_digit_hist_seg(c->out_keys.p, kw, d_bounds, 256, n, (uint64_t*)c->pass_hist.p, 1, st, shift1);
+    launch_digit_offsets_seg((const uint64_t*)c->pass_hist.p, d_bounds, doff, 1, 256, st);
+    CK(cudaMemcpyAsync(doff + 256 * 256, &hb[256], 8, cudaMemcpyHostToDevice, st));
+    uint32_t ep, *ctr;
+    TRY(hsk_next_epoch(c, st, &ep));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_onesweep_seg(c->out_keys.p, c->pair_alt_keys.p, (const uint32_t*)c->out_counts.p,
+                        (uint32_t*)c->pair_alt_counts.p, d_bounds, 256, (uint32_t)tiles, (const uint32_t*)c->seg.p, kw,
+                        shift1, doff, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), st));
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_range_sort(c->pair_alt_keys.p, (const uint32_t*)c->pair_alt_counts.p, c->out_keys.p,
+                      (uint32_t*)c->out_counts.p, doff, 256 * 256, kw, shift2, c->d_flag, ctr, c->num_sms, st);
+    CK(cudaGetLastError());
+    int too_big = 0;
+    CK(cudaMemcpyAsync(&too_big, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (too_big) {  // a sub-range over the on-chip capacity: the general path sorts all pairs
+        CK(cudaMemcpyAsync(c->out_keys.p, c->pair_alt_keys.p, n * kb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c->out_counts.p, c->pair_alt_counts.p, n * 4, cudaMemcpyDeviceToDevice, st));
+        return HSK_OK;
+    }
+    *done = true;
+    return HSK_OK;
+}
+
 // Split buckets [b0, b1) into at most C_want groups of roughly equal k-mer
 // counts; returns the first bucket of every group and b1.
 std::vector<uint32_t> hsk_group_buckets(const Supermers& S, uint32_t b0, uint32_t b1, uint32_t C_want) {
@@ -859,9 +923,13 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     TRY(hsk_local_overflow(c, sub_off, (uint32_t)(st3[1] & 0xFFFFFFFFull), ov_list, ov_list2, ov_list3, kw, shift0,
                            c->keys.p, (uint32_t*)c->alt.p, kcv, lo, hi, (uint64_t*)c->hist.p, H, c->d_max,
                            c->d_nlocal, nullptr, st, &left, &n_ov, &ov_keys));
+    // kept pairs in digit-major order (all groups' top digit 0, then 1, ...):
+    // the output is then partitioned by the top digit for stage S6
+    uint32_t* kc_t = ov_list;  // free again: the later steps list into ov_list2 / ov_list3
+    launch_transpose_kc(kcv, C, kc_t, c->num_sms * 8, st);
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));
-    launch_scan_u32(kcv, NS, kc_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
+    launch_scan_u32(kc_t, NS, kc_off, (uint64_t*)c->lb_status.p, ctr, ep, c->d_err, st);
     CK(cudaGetLastError());
     prof_mark(c, st, 4);
     uint64_t kept = 0;
@@ -870,10 +938,21 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     CK(cudaStreamSynchronize(st));
     O.n_distinct += st3[0];
     TRY(hsk_grow_output(c, O, O.n_pairs + kept, kw, st));
-    launch_compact(sub_off, kcv, kc_off, (uint32_t)NS, kw, c->keys.p, (const uint32_t*)c->alt.p,
+    launch_compact(sub_off, kcv, kc_off, (uint32_t)NS, C, kw, c->keys.p, (const uint32_t*)c->alt.p,
                    (char*)c->out_keys.p + O.n_pairs * kb, (uint32_t*)c->out_counts.p + O.n_pairs, kept, c->d_err,
                    c->num_sms * 8, st);
     CK(cudaGetLastError());
+    // where each top digit's pairs start (S6), valid while they are the only pairs
+    {
+        std::vector<uint64_t> at(257);
+        for (uint32_t d = 0; d <= 256; ++d) at[d] = (uint64_t)d * C;
+        TRY(hsk_ensure(c, c->s6_bounds, 2 * 257 * 8, false));
+        uint64_t* d_at = (uint64_t*)c->s6_bounds.p + 257;
+        CK(cudaMemcpyAsync(d_at, at.data(), 257 * 8, cudaMemcpyHostToDevice, st));
+        launch_gather_u64(kc_off, d_at, 257, (uint64_t*)c->s6_bounds.p, st);
+        CK(cudaGetLastError());
+        c->s6_digit_major = O.n_pairs == 0;
+    }
     O.n_pairs += kept;
     if (n_ov) {  // the sub-segments that did not fit: global radix passes, then S5
         TRY(hsk_ensure(c, c->batch_a, ov_keys * kb, false));
@@ -883,6 +962,7 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
         CK(cudaGetLastError());
         TRY(hsk_plain_sort(c, c->batch_a.p, nullptr, ov_keys, kw, key_bits, c->batch_b, nullptr, st));
         TRY(hsk_rle_chunk(c, c->batch_a.p, ov_keys, kw, lo, hi, H, (uint64_t*)c->hist.p, O, st));
+        c->s6_digit_major = false;  // pairs appended after the digit-major ones
     }
     c->last_ov_keys += ov_keys;
     prof_mark(c, st, 5);
@@ -927,6 +1007,7 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     R.n_supermers = S.n_records;
     std::vector<std::pair<uint32_t, uint32_t>> chunks;
     if (S.n_kmers > 0) TRY(hsk_plan_chunks(c, S, kw, chunks));
+    c->s6_digit_major = false;
     const int P = n_passes_for(2 * k);
     uint32_t total_segments = 0;
     bool unordered = false;
@@ -994,7 +1075,10 @@ int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, ui
     }
     if (total_segments > 1 || unordered) {
         NvtxRange r("S6 order");
-        TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st, hi));
+        bool done = false;
+        if (chunks.size() == 1 && c->cfg.local_sort && c->s6_digit_major)
+            TRY(order_pairs_msd(c, O.n_pairs, kw, 2 * k, st, &done));
+        if (!done) TRY(hsk_order_pairs(c, c->out_keys.p, (uint32_t*)c->out_counts.p, O.n_pairs, kw, 2 * k, st, hi));
     }
     prof_mark(c, st, 6);
     CK(cudaEventRecord(c->ev1, st));

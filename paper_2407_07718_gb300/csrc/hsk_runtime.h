@@ -271,6 +271,7 @@ struct hsk_ctx {
     uint64_t* d_ndesc = nullptr;
     uint64_t* d_nlocal = nullptr;   // distinct k-mers counted on chip
     uint64_t* d_ovstats = nullptr;  // per on-chip step: [2i] low half = sub-segments it listed, [2i+1] their keys
+    int* d_flag = nullptr;          // S6: a sub-range was over the on-chip capacity
     uint32_t* counters = nullptr;
     uint32_t ctr_used = 0;
     uint32_t epoch = 0;
@@ -286,6 +287,8 @@ struct hsk_ctx {
     DevBuf batch_a, batch_b, batch_c, batch_d;                     // on-chip path: overflow keys, tile map
     DevBuf pack_tab, pack_stat;                                    // packed sets: set tables, per-set statistics
     DevBuf ext_tab, ext_occ;                                       // extension information: key table, occurrence arrays
+    DevBuf s6_bounds;                                              // S6: where each top digit's kept pairs start
+    bool s6_digit_major = false;                                   // the output holds only digit-major pairs
 
     // tuned parameters (0 = built-in default); see hsk_tune.cu
     struct Tune {
@@ -328,7 +331,7 @@ struct hsk_ctx {
         return {&in_reads, &in_offsets, &pk, &iv, &rs, &cta_cnt, &cta_off, &bucket_kmers,
                 &bucket_rec, &records, &keys, &alt, &pass_hist, &digit_off, &lb_status, &seg, &heads, &rle_tiles,
                 &out_keys, &out_counts, &hist, &pair_alt_keys, &pair_alt_counts, &loc_tab, &batch_a,
-                &batch_b, &batch_c, &batch_d, &pack_tab, &pack_stat, &ext_tab, &ext_occ};
+                &batch_b, &batch_c, &batch_d, &pack_tab, &pack_stat, &ext_tab, &ext_occ, &s6_bounds};
     }
 };
 

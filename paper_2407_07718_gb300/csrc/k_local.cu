@@ -1059,10 +1059,13 @@ void launch_heavy_count(const uint64_t* sub_off, const uint32_t* list, uint32_t 
 // kept pairs -> output; listed sub-segments -> one array
 // ---------------------------------------------------------------------------
 // Warp w copies the kc[s] kept pairs of sub-segment s (from its range start)
-// to out_keys[out_off[s] ...], for s = w, w + warps, ...
+// to out_keys[out_off[s] ...], for s = w, w + warps, ...  With n_groups > 0
+// the offsets are digit-major: sub-segment s = group g, top digit d reads
+// out_off[d * n_groups + g] (all groups' digit-0 pairs first, then digit 1,
+// ...), so the output comes out partitioned by the top digit.
 template <typename K>
 __global__ void __launch_bounds__(256) k_compact(const u64* __restrict__ sub_off, const uint32_t* __restrict__ kc,
-                                                 const u64* __restrict__ out_off, uint32_t n_sub,
+                                                 const u64* __restrict__ out_off, uint32_t n_sub, uint32_t n_groups,
                                                  const K* __restrict__ keys, const uint32_t* __restrict__ kcount,
                                                  K* __restrict__ out_keys, uint32_t* __restrict__ out_counts,
                                                  u64 out_cap, int* err) {
@@ -1071,7 +1074,7 @@ __global__ void __launch_bounds__(256) k_compact(const u64* __restrict__ sub_off
     for (u64 s = (u64)blockIdx.x * 8 + (threadIdx.x >> 5); s < n_sub; s += nwarps) {
         const uint32_t n = kc[s];
         if (!n) continue;
-        const u64 src = sub_off[s], dst = out_off[s];
+        const u64 src = sub_off[s], dst = n_groups ? out_off[(s & 255) * n_groups + (s >> 8)] : out_off[s];
         if (dst + n > out_cap) {
             if (lane == 0) raise_error(err, HSK_DERR_BOUNDS);
             continue;
@@ -1084,19 +1087,35 @@ __global__ void __launch_bounds__(256) k_compact(const u64* __restrict__ sub_off
 }
 
 void launch_compact(const uint64_t* sub_off, const uint32_t* kc, const uint64_t* out_off, uint32_t n_sub,
-                    int key_words, const void* keys, const uint32_t* kcount, void* out_keys, uint32_t* out_counts,
-                    uint64_t out_cap, int* err, int grid, cudaStream_t st) {
+                    uint32_t n_groups, int key_words, const void* keys, const uint32_t* kcount, void* out_keys,
+                    uint32_t* out_counts, uint64_t out_cap, int* err, int grid, cudaStream_t st) {
     if (n_sub == 0) return;
     count_launch();
     uint64_t want = ((uint64_t)n_sub + 7) / 8;
     unsigned g = (unsigned)(want < (uint64_t)grid ? want : (uint64_t)grid);
     if (key_words == 1)
-        k_compact<u64><<<g, 256, 0, st>>>((const u64*)sub_off, kc, (const u64*)out_off, n_sub, (const u64*)keys,
-                                          kcount, (u64*)out_keys, out_counts, out_cap, err);
+        k_compact<u64><<<g, 256, 0, st>>>((const u64*)sub_off, kc, (const u64*)out_off, n_sub, n_groups,
+                                          (const u64*)keys, kcount, (u64*)out_keys, out_counts, out_cap, err);
     else
-        k_compact<key128><<<g, 256, 0, st>>>((const u64*)sub_off, kc, (const u64*)out_off, n_sub,
+        k_compact<key128><<<g, 256, 0, st>>>((const u64*)sub_off, kc, (const u64*)out_off, n_sub, n_groups,
                                              (const key128*)keys, kcount, (key128*)out_keys, out_counts, out_cap,
                                              err);
+}
+
+// kc_t[d * n_groups + g] = kc[g * 256 + d]: the kept counts in digit-major order
+__global__ void __launch_bounds__(256) k_transpose_kc(const uint32_t* __restrict__ kc, uint32_t n_groups,
+                                                      uint32_t* __restrict__ kc_t) {
+    const u64 n = (u64)n_groups * 256;
+    for (u64 s = (u64)blockIdx.x * 256 + threadIdx.x; s < n; s += (u64)gridDim.x * 256)
+        kc_t[(s & 255) * n_groups + (s >> 8)] = kc[s];
+}
+
+void launch_transpose_kc(const uint32_t* kc, uint32_t n_groups, uint32_t* kc_t, int grid, cudaStream_t st) {
+    if (n_groups == 0) return;
+    count_launch();
+    const u64 n = (u64)n_groups * 256;
+    const unsigned g = (unsigned)((n + 255) / 256 < (u64)grid ? (n + 255) / 256 : (u64)grid);
+    k_transpose_kc<<<g, 256, 0, st>>>(kc, n_groups, kc_t);
 }
 
 // One CTA: ov_pre[j] = sum of the sizes of listed sub-segments before j.

@@ -220,7 +220,7 @@ void launch_digit_hist(const void* keys, int key_words, uint64_t n, uint64_t* hi
 template <typename K>
 __global__ void __launch_bounds__(256) k_digit_hist_seg(const K* __restrict__ keys, const u64* __restrict__ key_base,
                                                         uint32_t C, u64 n, u64 chunk, u64* __restrict__ hist,
-                                                        int n_pass) {
+                                                        int n_pass, int shift0) {
     __shared__ uint32_t s_hist[MAX_PASS * RADIX];
     const u64 r0 = (u64)blockIdx.x * chunk;
     const u64 r1 = r0 + chunk < n ? r0 + chunk : n;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_digit_hist_seg(const K* __restrict__ ke
         __syncthreads();
         for (u64 i = a + threadIdx.x; i < b; i += 256) {
             const K key = keys[i];
-            for (int p = 0; p < n_pass; ++p) atomicAdd(&s_hist[p * RADIX + key_digit(key, 8 * p, 0xFF)], 1u);
+            for (int p = 0; p < n_pass; ++p) atomicAdd(&s_hist[p * RADIX + key_digit(key, shift0 + 8 * p, 0xFF)], 1u);
         }
         __syncthreads();
         u64* h = hist + (u64)c * n_pass * RADIX;
@@ -250,17 +250,17 @@ __global__ void __launch_bounds__(256) k_digit_hist_seg(const K* __restrict__ ke
 }
 
 void launch_digit_hist_seg(const void* keys, int key_words, const uint64_t* key_base, uint32_t C, uint64_t n,
-                           uint64_t* hist, int n_pass, cudaStream_t st) {
+                           uint64_t* hist, int n_pass, cudaStream_t st, int shift0) {
     if (n == 0 || C == 0) return;
     count_launch();
     const u64 chunk = 32768;
     const unsigned g = (unsigned)((n + chunk - 1) / chunk);
     if (key_words == 1)
         k_digit_hist_seg<u64><<<g, 256, 0, st>>>((const u64*)keys, (const u64*)key_base, C, n, chunk, (u64*)hist,
-                                                 n_pass);
+                                                 n_pass, shift0);
     else
         k_digit_hist_seg<key128><<<g, 256, 0, st>>>((const key128*)keys, (const u64*)key_base, C, n, chunk,
-                                                    (u64*)hist, n_pass);
+                                                    (u64*)hist, n_pass, shift0);
 }
 
 // dst[i] = src[idx[i]], i < n
@@ -753,6 +753,120 @@ void launch_onesweep_seg(const void* kin, void* kout, const uint32_t* vin, uint3
     else
         launch_pass_t<key128, true>(kin, kout, vin, vout, key_base, C, tmax, tile_start, shift, doff, status,
                                     tile_ctr, epoch, err, st);
+}
+
+// ---------------------------------------------------------------------------
+// S6 on chip: sort sub-ranges that already share their top digits
+// ---------------------------------------------------------------------------
+// After the kept pairs are laid out by their top digit and one segmented pass
+// has grouped each top-digit range by the second digit, every sub-range
+// holds pairs whose keys agree above bit `shift + 8`.  One CTA takes a
+// sub-range: it counts the keys' digit at `shift` (256 bins), places the
+// pairs bin by bin in shared memory, and writes each key to its sorted place:
+// the start of its bin plus the number of smaller keys in the bin (the keys
+// are distinct, so the places are too).
+constexpr int RS_NT = 512;
+template <typename K>
+struct RangeCfg;
+template <>
+struct RangeCfg<u64> {
+    static constexpr int CAP = 8192;  // 96 KB: two CTAs per SM
+};
+template <>
+struct RangeCfg<key128> {
+    static constexpr int CAP = 8192;  // 160 KB
+};
+uint32_t range_sort_cap(int key_words) { return key_words == 1 ? RangeCfg<u64>::CAP : RangeCfg<key128>::CAP; }
+
+template <typename K>
+__global__ void __launch_bounds__(RS_NT) k_range_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                      const u64* __restrict__ bounds, uint32_t n_ranges, int shift,
+                                                      int* too_big, uint32_t* claim) {
+    constexpr int CAP = RangeCfg<K>::CAP;
+    extern __shared__ __align__(16) unsigned char smem_rs[];
+    K* sk = reinterpret_cast<K*>(smem_rs);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(sk + CAP);
+    __shared__ uint32_t s_cnt[RADIX], s_start[RADIX], s_fill[RADIX];
+    __shared__ uint32_t s_scr[RS_NT / 32 + 1];
+    __shared__ uint32_t s_next;
+    const int tid = threadIdx.x;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_next = atomicAdd(claim, 1u);
+        if (tid < RADIX) s_cnt[tid] = 0;
+        __syncthreads();
+        const uint32_t r = s_next;
+        if (r >= n_ranges) break;
+        const u64 b = bounds[r], e = bounds[r + 1];
+        if (e <= b) continue;
+        const uint32_t n = (uint32_t)(e - b);
+        if (e - b > (u64)CAP) {
+            if (tid == 0) atomicExch(too_big, 1);
+            continue;
+        }
+        if (n == 1) {
+            if (tid == 0) {
+                kout[b] = kin[b];
+                vout[b] = vin[b];
+            }
+            continue;
+        }
+        for (uint32_t i = tid; i < n; i += RS_NT) atomicAdd(&s_cnt[key_digit(kin[b + i], shift, 0xFF)], 1u);
+        __syncthreads();
+        uint32_t tot;
+        const uint32_t c = tid < RADIX ? s_cnt[tid] : 0u;
+        const uint32_t ex = block_excl_sum<RS_NT, uint32_t>(c, s_scr, tot);
+        if (tid < RADIX) {
+            s_start[tid] = ex;
+            s_fill[tid] = ex;
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < n; i += RS_NT) {
+            const K key = kin[b + i];
+            const uint32_t at = atomicAdd(&s_fill[key_digit(key, shift, 0xFF)], 1u);
+            sk[at] = key;
+            sv[at] = vin[b + i];
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < n; i += RS_NT) {
+            const K key = sk[i];
+            const uint32_t d = key_digit(key, shift, 0xFF);
+            const uint32_t bs = s_start[d], be = bs + s_cnt[d];
+            uint32_t rank = 0;
+            for (uint32_t j = bs; j < be; ++j) rank += key_lt(sk[j], key) ? 1u : 0u;
+            kout[b + bs + rank] = key;
+            vout[b + bs + rank] = sv[i];
+        }
+    }
+}
+
+void launch_range_sort(const void* kin, const uint32_t* vin, void* kout, uint32_t* vout, const uint64_t* bounds,
+                       uint32_t n_ranges, int key_words, int shift, int* too_big, uint32_t* claim, int num_sms,
+                       cudaStream_t st) {
+    if (n_ranges == 0) return;
+    count_launch();
+    if (key_words == 1) {
+        const size_t dyn = (size_t)RangeCfg<u64>::CAP * 12;
+        cudaFuncSetAttribute(k_range_sort<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_range_sort<u64>, RS_NT, dyn);
+        if (occ < 1) occ = 1;
+        const uint64_t want = (uint64_t)num_sms * occ;
+        const unsigned g = (unsigned)(n_ranges < want ? n_ranges : want);
+        k_range_sort<u64><<<g, RS_NT, dyn, st>>>((const u64*)kin, vin, (u64*)kout, vout, (const u64*)bounds,
+                                                 n_ranges, shift, too_big, claim);
+    } else {
+        const size_t dyn = (size_t)RangeCfg<key128>::CAP * 20;
+        cudaFuncSetAttribute(k_range_sort<key128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_range_sort<key128>, RS_NT, dyn);
+        if (occ < 1) occ = 1;
+        const uint64_t want = (uint64_t)num_sms * occ;
+        const unsigned g = (unsigned)(n_ranges < want ? n_ranges : want);
+        k_range_sort<key128><<<g, RS_NT, dyn, st>>>((const key128*)kin, vin, (key128*)kout, vout,
+                                                    (const u64*)bounds, n_ranges, shift, too_big, claim);
+    }
 }
 
 // ---------------------------------------------------------------------------
