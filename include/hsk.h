@@ -171,8 +171,9 @@ int hsk_result_copy(hsk_ctx* ctx, const hsk_result* res, uint64_t* kmers_dst, ui
 /* Batched form: count n_jobs independent host-resident read sets.  The jobs
  * are queued, largest first, on the context's serving slots (child contexts
  * with their own streams and device arenas, running side by side).  A job of
- * at most the pack limit of bases (default 2^28) is counted together with
- * other queued small jobs of the same k, m, lo and hi by one pass of the
+ * at most the small-job limit of bases (default 2^28) is counted together
+ * with other queued small jobs of the same k, m, lo and hi, up to a pack of
+ * 2^28 bases by default (the autotuner picks both), by one pass of the
  * pipeline: their bases share one device buffer, each job owns a range of
  * minimizer buckets, and every launch serves all of them (Sec. 3.4's
  * independent tasks on shared workers).  Larger jobs run alone.  Each outs[i]

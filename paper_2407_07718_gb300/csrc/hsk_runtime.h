@@ -294,7 +294,7 @@ struct hsk_ctx {
     struct Tune {
         uint32_t group_div = 0;          // bucket-group keys = 256 x on-chip capacity / group_div (default 3)
         uint32_t plain_bucket_shift = 0; // large plain jobs use (4096 or 8192) >> shift buckets
-        uint64_t pack_bases = 0;         // bases of one pack at most (default 2^30)
+        uint64_t pack_bases = 0;         // bases of one pack at most (default 2^28)
         uint64_t pack_small = 0;         // sets with more bases run alone (default 2^28)
         int slots = 0;                   // serving slots (default 4)
     } tune;

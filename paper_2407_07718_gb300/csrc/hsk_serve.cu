@@ -80,7 +80,7 @@ static uint64_t pack_small_limit(const hsk_ctx* c) {
     return c->tune.pack_small ? c->tune.pack_small : (256ull << 20);
 }
 static uint64_t pack_bases_limit(const hsk_ctx* c) {
-    return c->tune.pack_bases ? c->tune.pack_bases : (1ull << 30);
+    return c->tune.pack_bases ? c->tune.pack_bases : (256ull << 20);
 }
 constexpr uint32_t PACK_MAX_SETS = 1024;
 

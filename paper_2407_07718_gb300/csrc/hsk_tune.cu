@@ -34,7 +34,7 @@ hsk_ctx::Tune defaults() {
     hsk_ctx::Tune t;
     t.group_div = 3;
     t.plain_bucket_shift = 0;
-    t.pack_bases = 1ull << 30;
+    t.pack_bases = 256ull << 20;
     t.pack_small = 256ull << 20;
     t.slots = 4;
     return t;
@@ -161,7 +161,9 @@ extern "C" int hsk_autotune(hsk_ctx* c, const hsk_job* jobs, uint32_t n_jobs, in
         const double first = best;
         const std::vector<uint32_t> divs = {2, 3, 4, 6};
         const std::vector<uint32_t> shifts = {0, 1};
-        const std::vector<uint64_t> packs = {256ull << 20, 512ull << 20, 1ull << 30, 2ull << 30};
+        // packs past 512 MB gained no throughput on the batched workload and
+        // lengthened served latency under load (a request waits for its pack)
+        const std::vector<uint64_t> packs = {64ull << 20, 128ull << 20, 256ull << 20, 512ull << 20};
         const std::vector<uint64_t> smalls = {64ull << 20, 256ull << 20, 1ull << 30};
         const std::vector<int> slots = {2, 3, 4, 6};
         // a candidate replaces the current value only when it is clearly faster
