@@ -322,7 +322,10 @@ template <>
 struct LocalCfg<key128, true> {
     static constexpr int CAP = 6144, STACK = 24, LIST = 368;   // 2 x 96 KB
 };
-constexpr int LS_D1 = 11;          // bits of the first partition's digit
+#ifndef HSK_LS_D1
+#define HSK_LS_D1 11
+#endif
+constexpr int LS_D1 = HSK_LS_D1;   // bits of the first partition's digit (compile-time knob)
 constexpr int LS_B1 = 1 << LS_D1;  // its bins (8 consecutive bins per thread)
 constexpr int LS_SMALL = 16;       // bins of at most this many keys: counted key by key
 constexpr int LS_MED = 256;        // bins of at most this many keys: rank sort by one warp
