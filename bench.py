@@ -55,7 +55,7 @@ NCU_PER_KEY = {
     # long-read workload, k=31: k_local_sort passes 0 + 1 (the heavy-hitter kernel does not
     # run at this scale), smsp__inst_executed.sum, DRAM bytes and shared-memory wavefronts
     # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) from the 0.1-scale case (149.6 M keys)
-    ("long_read", "96602f4d3cddc5e1"): {"inst": 11.4753, "dram": 8.3887, "smem_wavefronts": 2.3459},
+    ("long_read", "5ae756f122babc11"): {"inst": 11.4799, "dram": 8.3856, "smem_wavefronts": 2.3469},
 }
 # Warp schedulers per SM (Blackwell): each issues at most one warp instruction
 # per cycle; the issue peak is SMs (queried from the device) x this x the SM
@@ -135,6 +135,11 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            # nvidia-smi's start-up can hold the host's driver calls for up to
+            # a second; let it reach its first sample before anything is timed
+            t_end = time.time() + 3.0
+            while time.time() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
