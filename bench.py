@@ -115,6 +115,46 @@ def make_workload(name: str, scale: float):
     return rs, desc
 
 
+def e2e_parts(ctx, rs, pin_reads, pin_offs, e2e: dict, dev) -> dict:
+    """What one end-to-end call is made of: the device stages inside it (CUDA
+    events on its stream; S1/S2 overlap the input copy, so they include any
+    wait for it), the same host->device and device->host copies timed alone,
+    and the rest of the wall time (host work and synchronisation)."""
+    import torch
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    t0 = time.perf_counter()
+    ctx.count(pin_reads, pin_offs, rs.k, rs.m, rs.lo, rs.hi, copy=False)
+    wall = (time.perf_counter() - t0) * 1e3
+    stage_ms, _ = ctx.profile_read(reset=True)
+    ctx.profile(False)
+
+    def timed_copy(dst, src, reps=3):
+        dst.copy_(src, non_blocking=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    h_in = torch.from_numpy(pin_reads)  # shares the pinned pages
+    d_in = torch.empty(h_in.numel(), dtype=torch.uint8, device=dev)
+    h2d_ms = timed_copy(d_in, h_in)
+    del d_in
+    nb_out = max(int(e2e["d2h_bytes_per_step"]), 1)
+    d_out = torch.empty(nb_out, dtype=torch.uint8, device=dev)
+    h_out = torch.empty(nb_out, dtype=torch.uint8).pin_memory()
+    d2h_ms = timed_copy(h_out, d_out)
+    del d_out, h_out
+    dev_ms = float(sum(stage_ms))
+    return {"wall_ms": wall, "device_stages_ms": dev_ms, "host_and_copy_out_ms": wall - dev_ms,
+            "h2d_alone_ms": h2d_ms, "h2d_gbs": pin_reads.nbytes / h2d_ms / 1e6,
+            "d2h_alone_ms": d2h_ms, "d2h_gbs": nb_out / d2h_ms / 1e6,
+            "note": "one profiled hsk_count call; copies timed alone from/to pinned host memory"}
+
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
@@ -772,6 +812,7 @@ def main():
            "d2h_bytes_per_step": int(r.extra["n_pairs"] * (kb + 4) + 65536 * 8),
            "ms_per_step": dt * 1e3}
     assert r.n_windows == n_windows
+    e2e["parts"] = e2e_parts(ctx, rs, pin_reads, pin_offs, e2e, dev)
 
     ext_leg = None
     if rank == 0 and world == 1 and not args.no_ext:

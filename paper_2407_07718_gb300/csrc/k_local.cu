@@ -300,41 +300,54 @@ void launch_part(int mode, const uint64_t* records, const uint64_t* rec_base, co
 // ---------------------------------------------------------------------------
 // sort + count one sub-segment in shared memory
 // ---------------------------------------------------------------------------
+// Bins of at most ls_small<K>() keys are counted key by key (every key of
+// the bin compares itself with the others); larger ones through the
+// equal-to-first-key mask.  The best cut was measured per key width: 16 for
+// 64-bit keys (long-read workload: 8 -> 41.1 ms, 16 -> 31.8, 32 -> 35.5) and
+// 32 for 128-bit keys (short-read workload: 16 -> 35.6 ms, 32 -> 32.2).
+#ifndef HSK_LS_SMALL_U64
+#define HSK_LS_SMALL_U64 16
+#endif
+#ifndef HSK_LS_SMALL_U128
+#define HSK_LS_SMALL_U128 32
+#endif
+template <typename K>
+constexpr int ls_small() { return sizeof(K) == 8 ? HSK_LS_SMALL_U64 : HSK_LS_SMALL_U128; }
+
 // Capacity of one CTA's two shared-memory key buffers.  The first pass runs
 // 3 CTAs per SM; the second takes the sub-segments that did not fit, one CTA
 // per SM with most of the SM's shared memory.  STACK and LIST bound the open
-// bins (disjoint, > LS_MED keys each) and the bins over LS_SMALL keys.
+// bins (disjoint, > LS_MED keys each) and the bins over ls_small<K>() keys.
 template <typename K, bool BIG>
 struct LocalCfg;
 template <>
 struct LocalCfg<u64, false> {
-    static constexpr int CAP = 4096, STACK = 16, LIST = 256;  // 2 x 32 KB
+    static constexpr int CAP = 4096, STACK = 16, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 32 KB
 };
 template <>
 struct LocalCfg<key128, false> {
-    static constexpr int CAP = 2048, STACK = 16, LIST = 128;  // 2 x 32 KB
+    static constexpr int CAP = 2048, STACK = 16, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;  // 2 x 32 KB
 };
 template <>
 struct LocalCfg<u64, true> {
-    static constexpr int CAP = 12288, STACK = 48, LIST = 736;  // 2 x 96 KB
+    static constexpr int CAP = 12288, STACK = 48, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 96 KB
 };
 template <>
 struct LocalCfg<key128, true> {
-    static constexpr int CAP = 6144, STACK = 24, LIST = 368;   // 2 x 96 KB
+    static constexpr int CAP = 6144, STACK = 24, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;   // 2 x 96 KB
 };
 #ifndef HSK_LS_D1
 #define HSK_LS_D1 11
 #endif
 constexpr int LS_D1 = HSK_LS_D1;   // bits of the first partition's digit (compile-time knob)
 constexpr int LS_B1 = 1 << LS_D1;  // its bins (8 consecutive bins per thread)
-constexpr int LS_SMALL = 16;       // bins of at most this many keys: counted key by key
 constexpr int LS_MED = 256;        // bins of at most this many keys: rank sort by one warp
 constexpr int LS_PEEL = 8;         // distinct keys peeled off a bin before it is sorted
 constexpr int LS_HS = 128;         // count-histogram bins kept in shared memory
-// open bins are disjoint and hold > LS_MED keys; listed bins hold > LS_SMALL
+// open bins are disjoint and hold > LS_MED keys; listed bins hold > ls_small<K>()
 #define HSK_LS_CHECK(K, BIG)                                                                        \
     static_assert(LocalCfg<K, BIG>::CAP / (LS_MED + 1) < LocalCfg<K, BIG>::STACK, "stack too small"); \
-    static_assert(LocalCfg<K, BIG>::CAP / (LS_SMALL + 1) < LocalCfg<K, BIG>::LIST, "list too small")
+    static_assert(LocalCfg<K, BIG>::CAP / (ls_small<K>() + 1) < LocalCfg<K, BIG>::LIST, "list too small")
 HSK_LS_CHECK(u64, false);
 HSK_LS_CHECK(u64, true);
 HSK_LS_CHECK(key128, false);
@@ -359,7 +372,7 @@ struct LsBin {
 // equal share every digit and so one bin; a bin's runs are found without
 // ordering it: a key starts a run when no earlier key of the bin equals it,
 // and the run's count is the number of keys of the bin equal to it (bins of
-// <= LS_SMALL keys, one thread per key).  A warp takes larger bins by
+// <= ls_small<K>() keys, one thread per key).  A warp takes larger bins by
 // peeling off one distinct key at a time (warp_bin); what is left after
 // LS_PEEL peels is rank-sorted and scanned, or, past LS_MED keys,
 // partitioned again on the next 8-bit digit by the whole CTA.  Every run
@@ -717,7 +730,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                 v = B[i];
                 const uint32_t d = key_digit(v, s1, LS_B1 - 1);
                 const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
-                if (be - bs <= (uint32_t)LS_SMALL) {
+                if (be - bs <= (uint32_t)ls_small<K>()) {
                     head = true;
                     eqf = true;  // counted here: the mask marks it done
                     for (uint32_t j = bs; j < be; ++j)
@@ -750,7 +763,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                     v = B[i];
                     const uint32_t d = key_digit(v, s1, LS_B1 - 1);
                     const uint32_t be = s_cnt1[d], bs = d ? s_cnt1[d - 1] : 0u;
-                    if (be - bs > (uint32_t)LS_SMALL && be - bs <= (uint32_t)LS_MED) {
+                    if (be - bs > (uint32_t)ls_small<K>() && be - bs <= (uint32_t)LS_MED) {
                         head = true;
                         const uint32_t w0 = bs >> 5, w1 = (be - 1) >> 5;
                         for (uint32_t w = w0; w <= w1; ++w) {
@@ -850,8 +863,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
             __syncthreads();
             const uint32_t sb = bin.beg + ex;
             if (cnt == 1) emit(Y[sb], 1u);
-            else if (cnt > 1 && cnt <= (uint32_t)LS_SMALL) thread_bin(Y + sb, cnt, emit);
-            else if (cnt > (uint32_t)LS_SMALL)
+            else if (cnt > 1 && cnt <= (uint32_t)ls_small<K>()) thread_bin(Y + sb, cnt, emit);
+            else if (cnt > (uint32_t)ls_small<K>())
                 s_list[atomicAdd(&s_nl, 1)] = sb | (cnt << 16);
             __syncthreads();
             const int nl2 = s_nl;
