@@ -107,6 +107,37 @@ __device__ __forceinline__ uint32_t window_min(const uint32_t (&X)[NREG], int w,
     return d == 0 ? A[0] : min(A[0], seq_at<NREG>(A, 0, d, lane));
 }
 
+// Minimum of v over lanes [lane, 31] (suffix) and over [0, lane] (prefix).
+__device__ __forceinline__ uint32_t lane_suffix_min(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_down_sync(0xffffffffu, v, d);
+        if (lane + d < 32) v = min(v, o);
+    }
+    return v;
+}
+__device__ __forceinline__ uint32_t lane_prefix_min(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v = min(v, o);
+    }
+    return v;
+}
+
+// Window minimum for 33 <= w <= 65 (three score registers): a window that
+// starts at lane l of block 0 always runs past the block's end, so it is the
+// suffix of block 0 from l, then either a prefix of block 1 or all of block
+// 1 and a prefix of block 2 (van Herk / Gil-Werman with 32-lane blocks).
+// sm0 = suffix minima of block 0, pm1 / pm2 = prefix minima of blocks 1 / 2.
+__device__ __forceinline__ uint32_t window_min_wide(uint32_t sm0, uint32_t pm1, uint32_t pm2, int w, int lane) {
+    const int e = lane + w - 1;  // last position of the window, 32 <= e <= 95
+    const uint32_t a = __shfl_sync(0xffffffffu, pm1, (e - 32) & 31);
+    const uint32_t b = __shfl_sync(0xffffffffu, pm2, (e - 64) & 31);
+    const uint32_t full1 = __shfl_sync(0xffffffffu, pm1, 31);
+    return min(sm0, e < 64 ? a : min(full1, b));
+}
+
 // Bit t (most significant first) = OR of bits [t, t + L) of the 128-bit
 // value a:b, for t = 0..63 and 1 <= L <= 64: OR over windows of doubling
 // width, then two overlapping windows of that width.
@@ -234,6 +265,10 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
         uint32_t X[NREG];
 #pragma unroll
         for (int r = 0; r < NREG; ++r) X[r] = mmer_score<LEX>(wpk, 32 * r + lane, m, P.seed32);
+        // wide windows (three registers): prefix minima of block 1, carried
+        // from one step to the next as block 2's
+        uint32_t pm_next = 0;
+        if constexpr (NREG == 3) pm_next = lane_prefix_min(X[1], lane);
 
         int c_valid = 0, c_runstart = -1;   // carry from lane 31 of the previous step
         uint32_t c_b = 0;
@@ -262,7 +297,14 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
             const int lp = 32 * s + lane;
             const u64 p = p0 + lp;
             int valid = (p + k <= P.n_bases) && ((wval[lp >> 6] >> (63 - (lp & 63))) & 1);
-            const uint32_t mh = window_min<NREG>(X, w, lane);
+            uint32_t mh;
+            if constexpr (NREG == 3) {
+                const uint32_t pm2 = lane_prefix_min(X[2], lane);
+                mh = window_min_wide(lane_suffix_min(X[0], lane), pm_next, pm2, w, lane);
+                pm_next = pm2;
+            } else {
+                mh = window_min<NREG>(X, w, lane);
+            }
             const uint32_t b = bbase + (mh & bmask);
 
             if (MODE == SM_DUMP) {
