@@ -14,8 +14,11 @@
 // tile of 1024 consecutive window starts in 32 steps, lane l handling window
 // 32*s + l.  The packed bases and masks of the tile are staged in shared
 // memory with 128-bit loads.  Each lane computes one new m-mer score per step;
-// the window minimum over w = k-m+1 scores comes from a log-step doubling of
-// minima across lanes with shuffles (a sparse table in registers).  Supermer
+// the window minimum over w = k-m+1 scores comes from minima over 32-lane
+// blocks kept in registers: for w <= 33 the minima of runs of D = 2^L <= w
+// scores (doubling with shuffles, each block's computed once and carried to
+// the next step), for w > 33 suffix and prefix minima of the blocks (van
+// Herk / Gil-Werman with 32-lane blocks).  Supermer
 // cuts (bucket change, invalid window, cap of nmax k-mers, tile end) come
 // from ballots of run starts (the latest start at or before a lane is the
 // highest set bit below it).  The walk runs once (DESC): every
@@ -72,41 +75,6 @@ __device__ __forceinline__ uint32_t mmer_score(const u64* pk, int q, int m, uint
     else return fmix32((uint32_t)c ^ (uint32_t)(c >> 32) ^ seed);
 }
 
-// Value at index lane + d (0 <= d < 32) of the 32*NREG-long sequence held as
-// A[0..NREG) (A[r] holds indices 32r .. 32r+31), starting from register r.
-template <int NREG>
-__device__ __forceinline__ uint32_t seq_at(const uint32_t (&A)[NREG], int r, int d, int lane) {
-    int src = (lane + d) & 31;
-    uint32_t a = __shfl_sync(0xffffffffu, A[r], src);
-    uint32_t b = 0xffffffffu;
-    if (r + 1 < NREG) b = __shfl_sync(0xffffffffu, A[r + 1], src);
-    return lane + d < 32 ? a : b;
-}
-
-// min(X[lane .. lane + w - 1]) with X given as NREG registers, w <= 32*NREG - 31.
-template <int NREG>
-__device__ __forceinline__ uint32_t window_min(const uint32_t (&X)[NREG], int w, int lane) {
-    uint32_t A[NREG];
-#pragma unroll
-    for (int r = 0; r < NREG; ++r) A[r] = X[r];
-    int width = 1;
-    while (2 * width <= w) {
-        if (width == 32) {
-#pragma unroll
-            for (int r = 0; r < NREG; ++r) A[r] = min(A[r], r + 1 < NREG ? A[r + 1] : 0xffffffffu);
-        } else {
-            uint32_t nx[NREG];
-#pragma unroll
-            for (int r = 0; r < NREG; ++r) nx[r] = seq_at<NREG>(A, r, width, lane);
-#pragma unroll
-            for (int r = 0; r < NREG; ++r) A[r] = min(A[r], nx[r]);
-        }
-        width *= 2;
-    }
-    int d = w - width;  // 0 <= d < width <= 32 (d < 32 because w <= 64)
-    return d == 0 ? A[0] : min(A[0], seq_at<NREG>(A, 0, d, lane));
-}
-
 // Minimum of v over lanes [lane, 31] (suffix) and over [0, lane] (prefix).
 __device__ __forceinline__ uint32_t lane_suffix_min(uint32_t v, int lane) {
 #pragma unroll
@@ -121,6 +89,29 @@ __device__ __forceinline__ uint32_t lane_prefix_min(uint32_t v, int lane) {
     for (int d = 1; d < 32; d <<= 1) {
         const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
         if (lane >= d) v = min(v, o);
+    }
+    return v;
+}
+
+// min(v[lane .. lane + 2^L - 1]) within the block (lanes past 31 ignored).
+__device__ __forceinline__ uint32_t lane_range_min_trunc(uint32_t v, int L, int lane) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        if (j < L) {
+            const uint32_t o = __shfl_down_sync(0xffffffffu, v, 1 << j);
+            if (lane + (1 << j) < 32) v = min(v, o);
+        }
+    }
+    return v;
+}
+// min(v[0 .. lane]) for lanes below n (n <= 32; other lanes: partial).
+__device__ __forceinline__ uint32_t lane_prefix_min_upto(uint32_t v, int n, int lane) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        if ((1 << j) < n) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, v, 1 << j);
+            if (lane >= (1 << j)) v = min(v, o);
+        }
     }
     return v;
 }
@@ -269,6 +260,15 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
         // from one step to the next as block 2's
         uint32_t pm_next = 0;
         if constexpr (NREG == 3) pm_next = lane_prefix_min(X[1], lane);
+        // narrow windows (two registers, w <= 33): with D = 2^L <= w < 2D, a
+        // window is two overlapping runs of D scores.  t_cur = min over runs
+        // of D starting at each lane of block 0, counted within the block
+        // only; computed for each block when it enters as block 1, carried.
+        int nL = 0;
+        while ((2 << nL) <= w) ++nL;
+        const int nD = 1 << nL;
+        uint32_t t_cur = 0;
+        if constexpr (NREG == 2) t_cur = lane_range_min_trunc(X[0], nL, lane);
 
         int c_valid = 0, c_runstart = -1;   // carry from lane 31 of the previous step
         uint32_t c_b = 0;
@@ -303,7 +303,20 @@ __global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
                 mh = window_min_wide(lane_suffix_min(X[0], lane), pm_next, pm2, w, lane);
                 pm_next = pm2;
             } else {
-                mh = window_min<NREG>(X, w, lane);
+                // block 1's runs within block 1, and its prefix minima that
+                // complete block 0's runs reaching into it (lanes past 32 - D)
+                const uint32_t t_new = lane_range_min_trunc(X[1], nL, lane);
+                const uint32_t pm1 = lane_prefix_min_upto(X[1], nD - 1, lane);
+                const int i1 = lane + nD - 33;  // last lane of block 1 in this lane's run
+                const uint32_t pv = __shfl_sync(0xffffffffu, pm1, i1 & 31);
+                const uint32_t tc = i1 >= 0 ? min(t_cur, pv) : t_cur;
+                // the second run starts at q = lane + w - D (in block 1 when q >= 32,
+                // where its run lies inside block 1 because w <= 33)
+                const int q = lane + w - nD;
+                const uint32_t a = __shfl_sync(0xffffffffu, tc, q & 31);
+                const uint32_t b = __shfl_sync(0xffffffffu, t_new, (q - 32) & 31);
+                mh = min(tc, q < 32 ? a : b);
+                t_cur = t_new;
             }
             const uint32_t b = bbase + (mh & bmask);
 
