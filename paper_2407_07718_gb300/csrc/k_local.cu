@@ -100,6 +100,59 @@ struct TileWalk {
     }
 };
 
+// The bases of a record from base p on, two bits each, most significant
+// first: one 64-bit window of 32 bases, refilled from the record's words.
+struct RecBases {
+    u64 cur;
+    uint32_t wi, off, left;
+    __device__ __forceinline__ void start(const u64 (&W)[4], uint32_t p) {
+        wi = p >> 5;
+        off = (p & 31) * 2;
+        left = 32;
+        cur = funnel64(sel4(W, wi), sel4(W, wi + 1), off);
+    }
+    __device__ __forceinline__ uint32_t next(const u64 (&W)[4]) {
+        const uint32_t b = (uint32_t)(cur >> 62);
+        cur <<= 2;
+        if (--left == 0) {
+            ++wi;
+            left = 32;
+            cur = funnel64(sel4(W, wi), sel4(W, wi + 1), off);
+        }
+        return b;
+    }
+};
+
+// Top 8-bit digit of the canonical code of every k-mer of a record (k >= 4).
+// The canonical code is the smaller of the forward code and its reverse
+// complement, so its first four bases are the smaller of the forward k-mer's
+// first four bases and the reverse complement's first four (the k-mer's last
+// four bases, complemented, in reverse order).  Two 8-bit windows roll along
+// the record instead of the whole 2k-bit codes.
+__device__ __forceinline__ uint32_t revcomp4(uint32_t x) {
+    x = ~x & 0xFFu;
+    return ((x & 3u) << 6) | ((x & 0xCu) << 2) | ((x >> 2) & 0xCu) | (x >> 6);
+}
+template <typename F>
+__device__ __forceinline__ void record_top_digits(const u64 (&W)[4], uint32_t n, int k, F&& f) {
+    if (n == 0) return;
+    uint32_t fw = (uint32_t)(W[0] >> 56);  // bases 0..3
+    RecBases lb;
+    lb.start(W, (uint32_t)k - 4);           // bases k-4 .. k-1
+    uint32_t last = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) last = (last << 2) | lb.next(W);
+    uint32_t rc = revcomp4(last);
+    f(min(fw, rc));
+    RecBases fb;
+    fb.start(W, 4u);
+    for (uint32_t j = 1; j < n; ++j) {
+        fw = ((fw << 2) | fb.next(W)) & 0xFFu;
+        rc = (rc >> 2) | ((3u - lb.next(W)) << 6);
+        f(min(fw, rc));
+    }
+}
+
 // Work: one counter over all record tiles of all groups; tile g belongs to
 // group tile_seg[g] and is tile g - tile_base[group] of it.
 // MODE 0: sub_cnt[c * 256 + d] += keys of group c whose digit at `shift` is d.
@@ -172,10 +225,17 @@ __global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __
                     nk[i] = (uint32_t)(W[i][RW - 1] & 0xFF);
                 }
             }
+            if (k >= 4 && shift == 2 * k - 8) {  // the digit is the first four bases
 #pragma unroll
-            for (int i = 0; i < EXP_RPT; ++i)
-                record_kmers<WIDE>(W[i], nk[i], k,
-                                   [&](uint32_t, const K& key) { atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u); });
+                for (int i = 0; i < EXP_RPT; ++i)
+                    record_top_digits(W[i], nk[i], k, [&](uint32_t d) { atomicAdd(&s_cnt[d], 1u); });
+            } else {
+#pragma unroll
+                for (int i = 0; i < EXP_RPT; ++i)
+                    record_kmers<WIDE>(W[i], nk[i], k, [&](uint32_t, const K& key) {
+                        atomicAdd(&s_cnt[key_digit(key, shift, 0xFF)], 1u);
+                    });
+            }
             __syncthreads();
             const uint32_t v = s_cnt[tid];
             if (v) atomicAdd(sub_cnt + (u64)c * 256 + tid, v);
