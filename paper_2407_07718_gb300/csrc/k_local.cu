@@ -382,27 +382,31 @@ template <typename K, bool BIG>
 struct LocalCfg;
 template <>
 struct LocalCfg<u64, false> {
-    static constexpr int CAP = 4096, STACK = 16, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 32 KB
+    static constexpr int CAP = 4096, STACK = 33, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 32 KB
 };
 template <>
 struct LocalCfg<key128, false> {
-    static constexpr int CAP = 2048, STACK = 16, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;  // 2 x 32 KB
+    static constexpr int CAP = 2048, STACK = 17, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;  // 2 x 32 KB
 };
 template <>
 struct LocalCfg<u64, true> {
-    static constexpr int CAP = 12288, STACK = 48, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 96 KB
+    static constexpr int CAP = 12288, STACK = 97, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 96 KB
 };
 template <>
 struct LocalCfg<key128, true> {
-    static constexpr int CAP = 6144, STACK = 24, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;   // 2 x 96 KB
+    static constexpr int CAP = 6144, STACK = 49, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;   // 2 x 96 KB
 };
 #ifndef HSK_LS_D1
 #define HSK_LS_D1 11
 #endif
 constexpr int LS_D1 = HSK_LS_D1;   // bits of the first partition's digit (compile-time knob)
 constexpr int LS_B1 = 1 << LS_D1;  // its bins (8 consecutive bins per thread)
-constexpr int LS_MED = 256;        // bins of at most this many keys: rank sort by one warp
-constexpr int LS_PEEL = 8;         // distinct keys peeled off a bin before it is sorted
+// A warp peels up to LS_PEEL distinct keys off a larger bin; what is left is
+// rank-sorted when it holds at most LS_MED keys, else partitioned again.
+// Measured on the long-read workload (on-chip stage): LS_MED 256 / LS_PEEL 8
+// 31.8 ms, 128 / 8 30.3, 256 / 16 29.7, 128 / 32 29.0, 64 / 32 37.8.
+constexpr int LS_MED = 128;
+constexpr int LS_PEEL = 32;
 constexpr int LS_HS = 128;         // count-histogram bins kept in shared memory
 // open bins are disjoint and hold > LS_MED keys; listed bins hold > ls_small<K>()
 #define HSK_LS_CHECK(K, BIG)                                                                        \
