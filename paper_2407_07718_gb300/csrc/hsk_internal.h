@@ -28,6 +28,9 @@ void launch_encode_range(const char* reads, uint64_t n_bases, uint64_t b0, uint6
                          uint64_t* invalid, uint64_t n_packed_words, cudaStream_t st);
 constexpr uint64_t SM_TILE_BASES = 1024;   // windows per S2 warp tile
 constexpr uint64_t SM_TILE_REACH = 1280;   // bases past a tile's start that its walk reads
+// warps per CTA of the walk; one bucket-counter table per CTA in shared
+// memory, so more warps share it (16: short-read S2 17.9 -> 16.1 ms against 8)
+constexpr int SM_CTA_WARPS = 16;
 void launch_mark_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,
                         uint64_t* start_mask, int* err, cudaStream_t st);
 

@@ -427,7 +427,7 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
     const int nreg = P.w <= 33 ? 2 : 3;
     const int occ = supermer_max_ctas_per_sm(SM_DESC, wide, nreg, B);
     const uint64_t warp_tiles = (E.n_bases + 1023) / 1024;
-    uint64_t g = std::min<uint64_t>((uint64_t)c->num_sms * occ, (warp_tiles + 7) / 8);
+    uint64_t g = std::min<uint64_t>((uint64_t)c->num_sms * occ, (warp_tiles + SM_CTA_WARPS - 1) / SM_CTA_WARPS);
     P.grid = (uint32_t)std::max<uint64_t>(g, 1);
     TRY(hsk_ensure(c, c->bucket_kmers, (uint64_t)B * 8, false));
     TRY(hsk_ensure(c, c->bucket_rec, ((uint64_t)B + 1) * 8, false));
@@ -471,7 +471,7 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
                 if (t_end > t_done) {
                     P.tile_begin = t_done;
                     P.tile_end = t_end;
-                    P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(grid, (t_end - t_done + 7) / 8));
+                    P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(grid, (t_end - t_done + SM_CTA_WARPS - 1) / SM_CTA_WARPS));
                     launch_supermer(SM_DESC, P, st);
                     t_done = t_end;
                 }
@@ -1276,7 +1276,7 @@ extern "C" int hsk_stage_windows(hsk_ctx* c, const char* d_reads, const uint64_t
         SmParams P;
         fill_sm_params(c, E, k, m, 1, P);
         uint64_t warp_tiles = (n_bases + 1023) / 1024;
-        P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->num_sms * 4, (warp_tiles + 7) / 8));
+        P.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->num_sms * 4, (warp_tiles + SM_CTA_WARPS - 1) / SM_CTA_WARPS));
         P.dump_valid = d_valid;
         P.dump_key = d_key;
         P.dump_minhash = d_minhash;

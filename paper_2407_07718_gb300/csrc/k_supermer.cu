@@ -32,7 +32,7 @@
 
 namespace hsk {
 
-constexpr int SM_WARPS = 8;
+constexpr int SM_WARPS = SM_CTA_WARPS;
 constexpr int SM_STEPS = 32;
 constexpr int SM_TW = 32 * SM_STEPS;      // windows per warp tile
 constexpr int SM_PW = SM_TW / 32 + 6;     // packed words staged per warp (even)
@@ -157,7 +157,7 @@ __device__ __forceinline__ u64 make_desc(u64 pos, uint32_t n, uint32_t b) {
 }
 
 template <int MODE, bool WIDE, int NREG, bool LEX>
-__global__ void __launch_bounds__(256) k_supermer(const SmParams P) {
+__global__ void __launch_bounds__(SM_WARPS * 32) k_supermer(const SmParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     u64* s_pk = reinterpret_cast<u64*>(smem);
     u64* s_iv = s_pk + SM_WARPS * SM_PW;
@@ -404,7 +404,7 @@ static void launch_mode(const SmParams& p, cudaStream_t st) {
     do {                                                                                     \
         auto fn = p.lexical ? k_supermer<MODE, W, NR, true> : k_supermer<MODE, W, NR, false>; \
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
-        fn<<<grid, 256, sm, st>>>(p);                                                        \
+        fn<<<grid, SM_WARPS * 32, sm, st>>>(p);                                                        \
     } while (0)
     if (!wide && nreg == 2) HSK_SM_LAUNCH(false, 2);
     else if (!wide) HSK_SM_LAUNCH(false, 3);
@@ -427,7 +427,7 @@ int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets) 
                           : (nreg == 2 ? (const void*)k_supermer<SM_DESC, false, 2, false>
                                        : (const void*)k_supermer<SM_DESC, false, 3, false>);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, sm) != cudaSuccess) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, SM_WARPS * 32, sm) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
 
