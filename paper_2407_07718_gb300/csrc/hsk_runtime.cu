@@ -413,6 +413,7 @@ static void fill_sm_params(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t 
 
 // Count supermers per (bucket, CTA), scan to record offsets, scatter records.
 // With a set map the bases hold packed sets and B is the buckets of all sets.
+static_assert(HSK_MAX_BUCKETS == 8192, "the S2 walk's shared-memory limit is sized for 8192 buckets");
 int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Supermers& S, cudaStream_t st,
                   InputPipe* pipe, const SetMap* sets) {
     SmParams P;

@@ -43,6 +43,12 @@ static_assert(SM_TW == (int)SM_TILE_BASES, "tile size");
 static_assert(SM_PW * 32 <= (int)SM_TILE_REACH && SM_MW * 64 <= (int)SM_TILE_REACH,
               "a tile's staged words must lie within its declared reach");
 
+// The bucket table sets the walk's shared memory, so it differs from call to
+// call.  Serving slots launch the walk from several host threads at once, and
+// the per-kernel opt-in limit is process-wide: every thread sets it to the
+// size of the largest table (SM_MAX_BUCKETS buckets), never to its own, so
+// one thread cannot lower it under another's launch.
+constexpr uint32_t SM_MAX_BUCKETS = 8192;
 size_t supermer_smem_bytes(int mode, uint32_t n_buckets) {
     size_t s = (size_t)SM_WARPS * (SM_PW + 2 * SM_MW + SM_VW) * sizeof(u64);
     if (mode == SM_DESC) s += (size_t)SM_WARPS * SM_DBUF * sizeof(u64) + (size_t)n_buckets * 2 * sizeof(uint32_t);
@@ -396,6 +402,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_supermer(const SmParams P) {
 template <int MODE>
 static void launch_mode(const SmParams& p, cudaStream_t st) {
     size_t sm = supermer_smem_bytes(MODE, p.n_buckets);
+    const size_t sm_cap = supermer_smem_bytes(MODE, SM_MAX_BUCKETS);
     bool wide = p.k > 32;
     int nreg = (p.w <= 33) ? 2 : 3;
     unsigned grid = p.grid;
@@ -403,7 +410,7 @@ static void launch_mode(const SmParams& p, cudaStream_t st) {
 #define HSK_SM_LAUNCH(W, NR)                                                                 \
     do {                                                                                     \
         auto fn = p.lexical ? k_supermer<MODE, W, NR, true> : k_supermer<MODE, W, NR, false>; \
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cap);  \
         fn<<<grid, SM_WARPS * 32, sm, st>>>(p);                                                        \
     } while (0)
     if (!wide && nreg == 2) HSK_SM_LAUNCH(false, 2);
@@ -426,7 +433,7 @@ int supermer_max_ctas_per_sm(int mode, bool wide, int nreg, uint32_t n_buckets) 
                                        : (const void*)k_supermer<SM_DESC, true, 3, false>)
                           : (nreg == 2 ? (const void*)k_supermer<SM_DESC, false, 2, false>
                                        : (const void*)k_supermer<SM_DESC, false, 3, false>);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)supermer_smem_bytes(mode, SM_MAX_BUCKETS));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, SM_WARPS * 32, sm) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }

@@ -51,6 +51,8 @@ def test_batched_form_256_sets_bit_exact(hsk):
         _check_all(got, wants, labels)
         stats = ctx.pack_stats()
     assert stats["sets"] > 0, stats
+    # no packed pass may fail (a failed pass is redone set by set, which hides it)
+    assert stats["failed_passes"] == 0 and stats["alone"] == 0, stats
 
 
 def test_served_form_2000_requests_bit_exact(hsk):
@@ -71,4 +73,6 @@ def test_served_form_2000_requests_bit_exact(hsk):
             for t in tickets:
                 ctx.release(t)
             del made, got
-        assert ctx.pack_stats()["sets"] > 0
+        stats = ctx.pack_stats()
+    assert stats["sets"] > 0, stats
+    assert stats["failed_passes"] == 0 and stats["alone"] == 0, stats
