@@ -55,7 +55,7 @@ NCU_PER_KEY = {
     # long-read workload, k=31: k_local_sort passes 0 + 1 (the heavy-hitter kernel does not
     # run at this scale), smsp__inst_executed.sum, DRAM bytes and shared-memory wavefronts
     # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) from the 0.1-scale case (149.6 M keys)
-    ("long_read", "5ae756f122babc11"): {"inst": 11.4799, "dram": 8.3856, "smem_wavefronts": 2.3469},
+    ("long_read", "cc3a2b196fef378f"): {"inst": 10.2845, "dram": 8.3796, "smem_wavefronts": 2.267},
 }
 # Warp schedulers per SM (Blackwell): each issues at most one warp instruction
 # per cycle; the issue peak is SMs (queried from the device) x this x the SM
