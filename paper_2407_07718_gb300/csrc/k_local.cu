@@ -41,7 +41,11 @@ constexpr int LP_NT = 256;
 template <bool WIDE>
 struct PartCfg {
     static constexpr int RW = WIDE ? 4 : 2;            // words per supermer record
-    static constexpr int ROUND = WIDE ? 2048 : 4096;   // keys grouped per scatter round
+    // keys grouped per scatter round; with 64-bit keys a smaller round lets a
+    // fourth CTA fit an SM (long-read partition 11.55 -> 10.94 ms), with
+    // 128-bit keys it did not pay (14.4 -> 16.5 ms)
+    static constexpr int ROUND = 2048;
+    static constexpr int CTAS = WIDE ? 3 : 4;  // scatter-pass CTAs per SM
     static constexpr int LR = ROUND / LP_NT;           // keys per thread and round
 };
 static_assert(EXP_TILE == 4 * LP_NT, "a thread sums the k-mer counts of four records");
@@ -170,7 +174,7 @@ __device__ __forceinline__ void record_top_digits(const u64 (&W)[4], uint32_t n,
 // record leaves lanes idle while the warp's longest record is expanded; in
 // the count pass that costs less than cutting, in the scatter pass more.)
 template <bool WIDE, int MODE>
-__global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : 3) k_part(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
+__global__ void __launch_bounds__(LP_NT, MODE == 0 ? 4 : PartCfg<WIDE>::CTAS) k_part(const u64* __restrict__ rec, const u64* __restrict__ rec_base,
                                                 const u64* __restrict__ tile_base, const uint32_t* __restrict__ tile_seg,
                                                 uint32_t n_tiles, int k, int shift, uint32_t* tile_ctr,
                                                 uint32_t* __restrict__ sub_cnt, unsigned long long* cursor,
