@@ -143,9 +143,11 @@ void launch_part(int mode, const uint64_t* records, const uint64_t* rec_base, co
                  cudaStream_t st);
 uint32_t local_cap(int key_words);
 uint32_t local_cap_big(int key_words);
+// keys a sub-segment may hold in on-chip tier 0 (first pass), 1 or 2
+uint32_t local_cap_tier(int key_words, int tier);
 // grp_set: set of each group (packed sets; nullptr = one set), statistics
 // per set at hist + set * hist_len, max_count[set], n_distinct[set]
-void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, bool big, int shift0,
+void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, int tier, int shift0,
                        int key_words, void* keys, uint32_t* kcount, uint32_t* kc, uint32_t* ov_list,
                        uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
                        uint32_t* max_count, uint64_t* n_distinct, const uint32_t* grp_set, uint32_t* claim,

@@ -260,13 +260,14 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         memcpy(tseg.data() + nt, grp_set.data(), (size_t)C * 4);  // group -> set after the tile map
         TRY(hsk_ensure(c, c->keys, nk * kb, false));
         TRY(hsk_ensure(c, c->alt, nk * 4, false));
-        const size_t t32b = (5 * NS * 4 + 7) & ~(size_t)7;
+        const size_t t32b = (6 * NS * 4 + 7) & ~(size_t)7;
         TRY(hsk_ensure(c, c->loc_tab, t32b + (3 * NS + 2) * 8, false));
         uint32_t* sub_cnt = (uint32_t*)c->loc_tab.p;
         uint32_t* kcv = sub_cnt + NS;
         uint32_t* ov_list = kcv + NS;
         uint32_t* ov_list2 = ov_list + NS;
         uint32_t* ov_list3 = ov_list2 + NS;
+        uint32_t* ov_list_m = ov_list3 + NS;
         uint64_t* sub_off = (uint64_t*)((char*)c->loc_tab.p + t32b);
         uint64_t* cursor = sub_off + NS + 1;
         uint64_t* kc_off = cursor + NS;
@@ -294,9 +295,9 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         CK(cudaGetLastError());
         // S4/S5 on chip, statistics per set; the larger sub-segments take the
         // second pass and the heavy-hitter k-mer lists (as in the plain path)
-        CK(cudaMemsetAsync(c->d_nlocal, 0, 56, st));
+        CK(cudaMemsetAsync(c->d_nlocal, 0, 72, st));
         TRY(hsk_next_counter(c, st, &ctr));
-        launch_local_sort(sub_off, nullptr, (uint32_t)NS, false, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
+        launch_local_sort(sub_off, nullptr, (uint32_t)NS, 0, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
                           ov_list, c->d_ovstats, lo, hi, (uint64_t*)c->hist.p, H, d_max, d_distinct, d_grp_set, ctr,
                           c->d_err, c->num_sms, st);
         CK(cudaGetLastError());
@@ -306,7 +307,7 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
         uint32_t* left = nullptr;
         uint32_t n_ov = 0;
         uint64_t ov_keys = 0;
-        TRY(hsk_local_overflow(c, sub_off, (uint32_t)(st3[1] & 0xFFFFFFFFull), ov_list, ov_list2, ov_list3, kw,
+        TRY(hsk_local_overflow(c, sub_off, (uint32_t)(st3[1] & 0xFFFFFFFFull), ov_list, ov_list_m, ov_list2, ov_list3, kw,
                                shift0, c->keys.p, (uint32_t*)c->alt.p, kcv, lo, hi, (uint64_t*)c->hist.p, H, d_max,
                                d_distinct, d_grp_set, st, &left, &n_ov, &ov_keys));
         TRY(hsk_next_epoch(c, st, &ep));

@@ -801,42 +801,56 @@ int hsk_plan_chunks(hsk_ctx* c, const Supermers& S, int key_words,
 }
 
 // The first on-chip pass listed n_ov1 sub-segments over its capacity in
-// ov_list.  They take a second sort pass with three times the capacity; what
-// still does not fit -- tasks about nine times the mean sub-segment or more,
-// made of heavy hitters (Sec. 3.5) -- is folded into on-chip k-mer lists
-// (64-bit keys).  *left, *n_left, *left_keys receive the sub-segments none of
-// these could take (for the global radix passes) and their key count.  The
-// statistics words d_ovstats[0..5] hold {listed, keys} of the three steps.
-int hsk_local_overflow(hsk_ctx* c, const uint64_t* sub_off, uint32_t n_ov1, uint32_t* ov_list, uint32_t* ov_list2,
-                       uint32_t* ov_list3, int kw, int shift0, void* keys, uint32_t* kcount, uint32_t* kcv,
-                       uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t H, uint32_t* d_max, uint64_t* d_distinct,
-                       const uint32_t* grp_set, cudaStream_t st, uint32_t** left, uint32_t* n_left,
-                       uint64_t* left_keys) {
-    uint64_t w[6] = {0, 0, 0, 0, 0, 0};
+// ov_list.  They take a second sort pass with 1.5 times the capacity (tier 1,
+// two CTAs per SM), what still does not fit a third with three times it
+// (tier 2); what is larger still -- tasks about nine times the mean
+// sub-segment or more, made of heavy hitters (Sec. 3.5) -- is folded into
+// on-chip k-mer lists (64-bit keys).  *left, *n_left, *left_keys receive the
+// sub-segments none of these could take (for the global radix passes) and
+// their key count.  The statistics words d_ovstats[0..7] hold {listed, keys}
+// of the four steps; ov_list_m receives tier 1's list.
+int hsk_local_overflow(hsk_ctx* c, const uint64_t* sub_off, uint32_t n_ov1, uint32_t* ov_list, uint32_t* ov_list_m,
+                       uint32_t* ov_list2, uint32_t* ov_list3, int kw, int shift0, void* keys, uint32_t* kcount,
+                       uint32_t* kcv, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t H, uint32_t* d_max,
+                       uint64_t* d_distinct, const uint32_t* grp_set, cudaStream_t st, uint32_t** left,
+                       uint32_t* n_left, uint64_t* left_keys) {
+    uint64_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     *left = ov_list2;
     *n_left = 0;
     *left_keys = 0;
     if (!n_ov1) return HSK_OK;
     uint32_t* ctr;
     TRY(hsk_next_counter(c, st, &ctr));
-    launch_local_sort(sub_off, ov_list, n_ov1, true, shift0, kw, keys, kcount, kcv, ov_list2, c->d_ovstats + 2, lo,
+    launch_local_sort(sub_off, ov_list, n_ov1, 1, shift0, kw, keys, kcount, kcv, ov_list_m, c->d_ovstats + 2, lo,
                       hi, hist, H, d_max, d_distinct, grp_set, ctr, c->d_err, c->num_sms, st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(w, c->d_ovstats, sizeof(w), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const uint32_t n_ov2 = (uint32_t)(w[2] & 0xFFFFFFFFull);
-    *n_left = n_ov2;
+    const uint32_t n_ovm = (uint32_t)(w[2] & 0xFFFFFFFFull);
+    *left = ov_list_m;
+    *n_left = n_ovm;
     *left_keys = w[3];
+    if (!n_ovm) return HSK_OK;
+    TRY(hsk_next_counter(c, st, &ctr));
+    launch_local_sort(sub_off, ov_list_m, n_ovm, 2, shift0, kw, keys, kcount, kcv, ov_list2, c->d_ovstats + 4, lo,
+                      hi, hist, H, d_max, d_distinct, grp_set, ctr, c->d_err, c->num_sms, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(w, c->d_ovstats, sizeof(w), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t n_ov2 = (uint32_t)(w[4] & 0xFFFFFFFFull);
+    *left = ov_list2;
+    *n_left = n_ov2;
+    *left_keys = w[5];
     if (n_ov2 && kw == 1) {
         TRY(hsk_next_counter(c, st, &ctr));
-        launch_heavy_count(sub_off, ov_list2, n_ov2, keys, kcount, kcv, ov_list3, c->d_ovstats + 4, lo, hi, hist, H,
+        launch_heavy_count(sub_off, ov_list2, n_ov2, keys, kcount, kcv, ov_list3, c->d_ovstats + 6, lo, hi, hist, H,
                            d_max, d_distinct, grp_set, ctr, c->d_err, c->num_sms, st);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(w, c->d_ovstats, sizeof(w), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         *left = ov_list3;
-        *n_left = (uint32_t)(w[4] & 0xFFFFFFFFull);
-        *left_keys = w[5];
+        *n_left = (uint32_t)(w[6] & 0xFFFFFFFFull);
+        *left_keys = w[7];
     }
     return HSK_OK;
 }
@@ -872,15 +886,17 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
         for (uint64_t t = tbase[i]; t < tbase[i + 1]; ++t) tseg[t] = i;
     TRY(hsk_ensure(c, c->keys, nk * kb, false));
     TRY(hsk_ensure(c, c->alt, nk * 4, false));  // counts of the kept pairs
-    // sub-segment tables: sub_cnt | kc | ov_list | ov_list2 | ov_list3 (u32[NS]
-    // each), then sub_off (NS + 1) | cursor (NS) | kc_off (NS + 1) (u64)
-    const size_t t32 = (5 * NS * 4 + 7) & ~(size_t)7;
+    // sub-segment tables: sub_cnt | kc | ov_list | ov_list2 | ov_list3 |
+    // ov_list_m (u32[NS] each), then sub_off (NS + 1) | cursor (NS) | kc_off
+    // (NS + 1) (u64)
+    const size_t t32 = (6 * NS * 4 + 7) & ~(size_t)7;
     TRY(hsk_ensure(c, c->loc_tab, t32 + (3 * NS + 2) * 8, false));
     uint32_t* sub_cnt = (uint32_t*)c->loc_tab.p;
     uint32_t* kcv = sub_cnt + NS;
     uint32_t* ov_list = kcv + NS;
     uint32_t* ov_list2 = ov_list + NS;
     uint32_t* ov_list3 = ov_list2 + NS;
+    uint32_t* ov_list_m = ov_list3 + NS;
     uint64_t* sub_off = (uint64_t*)((char*)c->loc_tab.p + t32);
     uint64_t* cursor = sub_off + NS + 1;
     uint64_t* kc_off = cursor + NS;
@@ -909,9 +925,9 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     // sort and count on chip; the sub-segments that do not fit go to a second
     // pass with three times the capacity, then to heavy-hitter k-mer lists,
     // and what none of these takes to the global radix passes
-    CK(cudaMemsetAsync(c->d_nlocal, 0, 56, st));  // distinct, then {listed, keys} of the three steps
+    CK(cudaMemsetAsync(c->d_nlocal, 0, 72, st));  // distinct, then {listed, keys} of the four steps
     TRY(hsk_next_counter(c, st, &ctr));
-    launch_local_sort(sub_off, nullptr, (uint32_t)NS, false, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
+    launch_local_sort(sub_off, nullptr, (uint32_t)NS, 0, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,
                       ov_list, c->d_ovstats, lo, hi, (uint64_t*)c->hist.p, H, c->d_max, c->d_nlocal, nullptr, ctr, c->d_err,
                       c->num_sms, st);
     CK(cudaGetLastError());
@@ -921,12 +937,12 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
     uint32_t* left = nullptr;
     uint32_t n_ov = 0;
     uint64_t ov_keys = 0;
-    TRY(hsk_local_overflow(c, sub_off, (uint32_t)(st3[1] & 0xFFFFFFFFull), ov_list, ov_list2, ov_list3, kw, shift0,
+    TRY(hsk_local_overflow(c, sub_off, (uint32_t)(st3[1] & 0xFFFFFFFFull), ov_list, ov_list_m, ov_list2, ov_list3, kw, shift0,
                            c->keys.p, (uint32_t*)c->alt.p, kcv, lo, hi, (uint64_t*)c->hist.p, H, c->d_max,
                            c->d_nlocal, nullptr, st, &left, &n_ov, &ov_keys));
     // kept pairs in digit-major order (all groups' top digit 0, then 1, ...):
     // the output is then partitioned by the top digit for stage S6
-    uint32_t* kc_t = ov_list;  // free again: the later steps list into ov_list2 / ov_list3
+    uint32_t* kc_t = ov_list;  // free again: the later steps list into ov_list_m / ov_list2 / ov_list3
     launch_transpose_kc(kcv, C, kc_t, c->num_sms * 8, st);
     TRY(hsk_next_epoch(c, st, &ep));
     TRY(hsk_next_counter(c, st, &ctr));

@@ -406,11 +406,11 @@ int hsk_supermers(hsk_ctx* c, const Encoded& E, int k, int m, uint32_t B, Superm
 uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k);
 int hsk_plain_sort(hsk_ctx* c, void* keys, uint32_t* vals, uint64_t n, int key_words, int key_bits, DevBuf& alt_keys,
                    DevBuf* alt_vals, cudaStream_t st);
-int hsk_local_overflow(hsk_ctx* c, const uint64_t* sub_off, uint32_t n_ov1, uint32_t* ov_list, uint32_t* ov_list2,
-                       uint32_t* ov_list3, int kw, int shift0, void* keys, uint32_t* kcount, uint32_t* kcv,
-                       uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t H, uint32_t* d_max, uint64_t* d_distinct,
-                       const uint32_t* grp_set, cudaStream_t st, uint32_t** left, uint32_t* n_left,
-                       uint64_t* left_keys);
+int hsk_local_overflow(hsk_ctx* c, const uint64_t* sub_off, uint32_t n_ov1, uint32_t* ov_list, uint32_t* ov_list_m,
+                       uint32_t* ov_list2, uint32_t* ov_list3, int kw, int shift0, void* keys, uint32_t* kcount,
+                       uint32_t* kcv, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t H, uint32_t* d_max,
+                       uint64_t* d_distinct, const uint32_t* grp_set, cudaStream_t st, uint32_t** left,
+                       uint32_t* n_left, uint64_t* left_keys);
 int hsk_run_count(hsk_ctx* c, const char* d_reads, const uint64_t* d_offsets, uint64_t n_reads,
                   uint64_t n_bases, int k, int m, uint32_t lo, uint32_t hi, cudaStream_t st,
                   DevResult& R, InputPipe* pipe = nullptr);

@@ -378,27 +378,44 @@ void launch_part(int mode, const uint64_t* records, const uint64_t* rec_base, co
 template <typename K>
 constexpr int ls_small() { return sizeof(K) == 8 ? HSK_LS_SMALL_U64 : HSK_LS_SMALL_U128; }
 
-// Capacity of one CTA's two shared-memory key buffers.  The first pass runs
-// 3 CTAs per SM; the second takes the sub-segments that did not fit, one CTA
-// per SM with most of the SM's shared memory.  STACK and LIST bound the open
-// bins (disjoint, > LS_MED keys each) and the bins over ls_small<K>() keys.
-template <typename K, bool BIG>
+// Capacity of one CTA's two shared-memory key buffers, per tier.  Tier 0
+// (the first pass) runs 3 CTAs per SM.  The sub-segments that do not fit go
+// to tier 1, 1.5 times the capacity with two CTAs per SM, and what does not
+// fit there to tier 2, three times the capacity with one 512-thread CTA per
+// SM.  (Tier 1 took the long-read workload's second-pass keys at about twice
+// the rate of tier 2, whose single CTA per SM leaves the SM idle while its
+// warps wait at barriers.)  STACK and LIST bound the open bins (disjoint,
+// > LS_MED keys each) and the bins over ls_small<K>() keys.
+template <typename K, int TIER>
 struct LocalCfg;
 template <>
-struct LocalCfg<u64, false> {
+struct LocalCfg<u64, 0> {
     static constexpr int CAP = 4096, STACK = 33, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 32 KB
 };
 template <>
-struct LocalCfg<key128, false> {
+struct LocalCfg<key128, 0> {
     static constexpr int CAP = 2048, STACK = 17, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;  // 2 x 32 KB
 };
 template <>
-struct LocalCfg<u64, true> {
+struct LocalCfg<u64, 1> {
+    static constexpr int CAP = 6144, STACK = 49, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 48 KB
+};
+template <>
+struct LocalCfg<key128, 1> {
+    static constexpr int CAP = 3072, STACK = 25, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;  // 2 x 48 KB
+};
+template <>
+struct LocalCfg<u64, 2> {
     static constexpr int CAP = 12288, STACK = 97, LIST = CAP / (HSK_LS_SMALL_U64 + 1) + 1;  // 2 x 96 KB
 };
 template <>
-struct LocalCfg<key128, true> {
+struct LocalCfg<key128, 2> {
     static constexpr int CAP = 6144, STACK = 49, LIST = CAP / (HSK_LS_SMALL_U128 + 1) + 1;   // 2 x 96 KB
+};
+template <int TIER>
+struct TierCfg {
+    static constexpr int NT = TIER == 2 ? 512 : 256;          // threads per CTA
+    static constexpr int CTAS = TIER == 0 ? 3 : TIER == 1 ? 2 : 1;  // CTAs per SM
 };
 #ifndef HSK_LS_D1
 #define HSK_LS_D1 11
@@ -413,22 +430,24 @@ constexpr int LS_MED = 128;
 constexpr int LS_PEEL = 32;
 constexpr int LS_HS = 128;         // count-histogram bins kept in shared memory
 // open bins are disjoint and hold > LS_MED keys; listed bins hold > ls_small<K>()
-#define HSK_LS_CHECK(K, BIG)                                                                        \
-    static_assert(LocalCfg<K, BIG>::CAP / (LS_MED + 1) < LocalCfg<K, BIG>::STACK, "stack too small"); \
-    static_assert(LocalCfg<K, BIG>::CAP / (ls_small<K>() + 1) < LocalCfg<K, BIG>::LIST, "list too small")
-HSK_LS_CHECK(u64, false);
-HSK_LS_CHECK(u64, true);
-HSK_LS_CHECK(key128, false);
-HSK_LS_CHECK(key128, true);
+#define HSK_LS_CHECK(K, T)                                                                        \
+    static_assert(LocalCfg<K, T>::CAP / (LS_MED + 1) < LocalCfg<K, T>::STACK, "stack too small"); \
+    static_assert(LocalCfg<K, T>::CAP / (ls_small<K>() + 1) < LocalCfg<K, T>::LIST, "list too small")
+HSK_LS_CHECK(u64, 0);
+HSK_LS_CHECK(u64, 1);
+HSK_LS_CHECK(u64, 2);
+HSK_LS_CHECK(key128, 0);
+HSK_LS_CHECK(key128, 1);
+HSK_LS_CHECK(key128, 2);
 
-uint32_t local_cap(int key_words) {
-    return key_words == 1 ? LocalCfg<u64, false>::CAP : LocalCfg<key128, false>::CAP;
+uint32_t local_cap_tier(int key_words, int tier) {
+    if (key_words == 1) return tier == 0 ? LocalCfg<u64, 0>::CAP : tier == 1 ? LocalCfg<u64, 1>::CAP : LocalCfg<u64, 2>::CAP;
+    return tier == 0 ? LocalCfg<key128, 0>::CAP : tier == 1 ? LocalCfg<key128, 1>::CAP : LocalCfg<key128, 2>::CAP;
 }
-uint32_t local_cap_big(int key_words) {
-    return key_words == 1 ? LocalCfg<u64, true>::CAP : LocalCfg<key128, true>::CAP;
-}
-static size_t local_smem_bytes(int key_words, bool big) {
-    return (size_t)2 * (big ? local_cap_big(key_words) : local_cap(key_words)) * 8 * key_words;
+uint32_t local_cap(int key_words) { return local_cap_tier(key_words, 0); }
+uint32_t local_cap_big(int key_words) { return local_cap_tier(key_words, 2); }
+static size_t local_smem_bytes(int key_words, int tier) {
+    return (size_t)2 * local_cap_tier(key_words, tier) * 8 * key_words;
 }
 
 struct LsBin {
@@ -579,8 +598,8 @@ __device__ __forceinline__ void ls_prefetch(K (&pf)[PFN], const K* keys, const u
 // histogram hist + set * hist_len, n_distinct[set] and max_count[set].  A CTA
 // takes sub-segments in ascending order, so the sets it meets ascend too; it
 // keeps one set's statistics on chip and flushes them when the set changes.
-template <typename K, bool BIG>
-__global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(const u64* __restrict__ sub_off,
+template <typename K, int TIER>
+__global__ void __launch_bounds__(TierCfg<TIER>::NT, TierCfg<TIER>::CTAS) k_local_sort(const u64* __restrict__ sub_off,
                                                       const uint32_t* __restrict__ only, uint32_t n_sub, int shift0,
                                                       K* keys, uint32_t* __restrict__ kcount,
                                                       uint32_t* __restrict__ kc, uint32_t* __restrict__ ov_list,
@@ -589,9 +608,9 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
                                                       uint32_t* max_count, unsigned long long* n_distinct,
                                                       const uint32_t* __restrict__ grp_set, uint32_t* claim,
                                                       int* err) {
-    using Cfg = LocalCfg<K, BIG>;
+    using Cfg = LocalCfg<K, TIER>;
     constexpr int CAP = Cfg::CAP;
-    constexpr int NT = BIG ? 512 : 256;   // threads
+    constexpr int NT = TierCfg<TIER>::NT;   // threads
     constexpr int BPT = LS_B1 / NT;       // first-partition bins per thread
     extern __shared__ __align__(16) unsigned char smem_local[];
     K* A = reinterpret_cast<K*>(smem_local);
@@ -681,7 +700,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
     };
     // Sub-segments are claimed one at a time; the next one's keys are loaded
     // into registers while the current one is sorted (first pass only).
-    constexpr int PF = BIG ? 0 : CAP / NT;
+    constexpr int PF = TIER == 0 ? CAP / NT : 0;
     constexpr int PFN = PF > 0 ? PF : 1;
     K pf[PFN];
     // the first partition's counters start at zero; each sub-segment clears
@@ -954,18 +973,18 @@ __global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 3) k_local_sort(con
     if (cur_set != 0xFFFFFFFFu) flush_stats(cur_set);
 }
 
-void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, bool big, int shift0,
+void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n_sub, int tier, int shift0,
                        int key_words, void* keys, uint32_t* kcount, uint32_t* kc, uint32_t* ov_list,
                        uint64_t* ov_stats, uint32_t lo, uint32_t hi, uint64_t* hist, uint32_t hist_len,
                        uint32_t* max_count, uint64_t* n_distinct, const uint32_t* grp_set, uint32_t* claim,
                        int* err, int num_sms, cudaStream_t st) {
     if (n_sub == 0) return;
     count_launch();
-    const size_t dyn = local_smem_bytes(key_words, big);
+    const size_t dyn = local_smem_bytes(key_words, tier);
+    const int nt = tier == 2 ? TierCfg<2>::NT : TierCfg<0>::NT;
     auto go = [&](auto kern, auto* kp) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         int occ = 0;
-        const int nt = big ? 512 : 256;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, dyn);
         if (occ < 1) occ = 1;
         uint64_t want = n_sub;
@@ -976,11 +995,13 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
                                               max_count, (unsigned long long*)n_distinct, grp_set, claim, err);
     };
     if (key_words == 1) {
-        if (big) go(k_local_sort<u64, true>, (u64*)keys);
-        else go(k_local_sort<u64, false>, (u64*)keys);
+        if (tier == 2) go(k_local_sort<u64, 2>, (u64*)keys);
+        else if (tier == 1) go(k_local_sort<u64, 1>, (u64*)keys);
+        else go(k_local_sort<u64, 0>, (u64*)keys);
     } else {
-        if (big) go(k_local_sort<key128, true>, (key128*)keys);
-        else go(k_local_sort<key128, false>, (key128*)keys);
+        if (tier == 2) go(k_local_sort<key128, 2>, (key128*)keys);
+        else if (tier == 1) go(k_local_sort<key128, 1>, (key128*)keys);
+        else go(k_local_sort<key128, 0>, (key128*)keys);
     }
 }
 
