@@ -163,6 +163,9 @@ extern "C" int hsk_create(hsk_ctx** out, const hsk_config* cfg_in) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg.device);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
+        int prio_least = 0, prio_greatest = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->hstream, cudaStreamNonBlocking, prio_greatest);
         for (int i = 0; i < HSK_MAX_PIPE && e == cudaSuccess; ++i)
             e = cudaEventCreateWithFlags(&c->pipe_ev[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -212,6 +215,10 @@ extern "C" void hsk_destroy(hsk_ctx* c) {
     if (c->cstream) {
         cudaStreamSynchronize(c->cstream);
         cudaStreamDestroy(c->cstream);
+    }
+    if (c->hstream) {
+        cudaStreamSynchronize(c->hstream);
+        cudaStreamDestroy(c->hstream);
     }
     for (int i = 0; i < HSK_MAX_PIPE; ++i)
         if (c->pipe_ev[i]) cudaEventDestroy(c->pipe_ev[i]);

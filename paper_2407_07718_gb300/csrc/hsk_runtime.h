@@ -255,6 +255,7 @@ struct hsk_ctx {
     int num_sms = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cstream = nullptr;  // input copies of host-input counting
+    cudaStream_t hstream = nullptr;  // highest priority: a serving slot's jobs too large to pack
     cudaEvent_t pipe_ev[HSK_MAX_PIPE] = {};
     cudaStream_t zst = nullptr;  // stream of the call in progress (orders zero-fills)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

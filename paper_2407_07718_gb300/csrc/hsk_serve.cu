@@ -205,9 +205,14 @@ static void worker_main(hsk_ctx* parent, ServeState* S, int slot) {
         std::vector<std::string> errs(group.size());
         if (group.size() == 1) {
             const hsk_job job = group[0]->job;
+            // A job too large to pack runs on the slot's highest-priority
+            // stream: its blocks are dispatched before those of the packs on
+            // the other slots, so it runs near its alone time (the tail of the
+            // latency distribution) while the packs fill the gaps.
+            cudaStream_t js = !group[0]->packable && c->hstream ? c->hstream : c->stream;
             rcs[0] = hsk_guarded(c, [&]() -> int {
                 return hsk_count_host_on(c, job.reads, job.offsets, job.n_reads, job.k, job.m, job.lo, job.hi,
-                                         c->stream, c->in_reads, c->in_offsets, hrs[0]);
+                                         js, c->in_reads, c->in_offsets, hrs[0]);
             });
             if (rcs[0] != HSK_OK) errs[0] = c->err_msg;
         } else {
