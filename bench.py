@@ -830,7 +830,11 @@ def main():
     del d_reads, d_offs
     forms = {}
     def leg(name, fn):  # each extra leg is also logged to stderr as soon as it ends
+        # the SM clocks over the whole leg, so that legs of different runs can be compared
+        sampler_leg = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+        sampler_leg.start()
         forms[name] = fn()
+        forms[name]["clocks"] = sampler_leg.stop()
         print(json.dumps({name: forms[name]}), file=sys.stderr, flush=True)
 
     if rank == 0 and world == 1 and args.second_workload not in ("none", args.workload):
