@@ -46,16 +46,16 @@ UNIT = "k-mers/s"
 # Per-key counters of the dominant kernel from one ncu capture, keyed by the
 # workload and the SHA-256 (first 16 hex digits) of the kernel's source file
 # at capture time; used only while that source is unchanged.
-#   inst  : warp instructions issued per key (both on-chip passes)
-#   dram  : DRAM bytes read + written per key (both passes)
-#   smem_wavefronts : shared-memory wavefronts per key (both passes); an SM's
+#   inst  : warp instructions issued per key (all on-chip tiers)
+#   dram  : DRAM bytes read + written per key (all tiers)
+#   smem_wavefronts : shared-memory wavefronts per key (all tiers); an SM's
 #           shared-memory pipe processes at most one wavefront per cycle
 # The commands that produced them are in profiles/.
 NCU_PER_KEY = {
-    # long-read workload, k=31: k_local_sort passes 0 + 1 (the heavy-hitter kernel does not
+    # long-read workload, k=31: k_local_sort tiers 0, 1 and 2 (the heavy-hitter kernel does not
     # run at this scale), smsp__inst_executed.sum, DRAM bytes and shared-memory wavefronts
     # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) from the 0.1-scale case (149.6 M keys)
-    ("long_read", "cc3a2b196fef378f"): {"inst": 10.2845, "dram": 8.3796, "smem_wavefronts": 2.267},
+    ("long_read", "bebf6f76bbefbe71"): {"inst": 10.1611, "dram": 8.3749, "smem_wavefronts": 2.2143},
 }
 # Warp schedulers per SM (Blackwell): each issues at most one warp instruction
 # per cycle; the issue peak is SMs (queried from the device) x this x the SM
@@ -745,7 +745,7 @@ def main():
                     "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs copy bandwidth)",
                     "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms}
     else:
-        # on-chip path: the sub-segment sort (k_local_sort, both passes) reads
+        # on-chip path: the sub-segment sort (k_local_sort, all tiers) reads
         # every key once and writes the kept pairs; it is bound by instruction
         # issue and shared-memory latency, so its roofline is the issue rate
         launch_ms = stage_ms[4] / args.steps
@@ -760,7 +760,7 @@ def main():
         wav = cnt.get("smem_wavefronts") * n_windows if cnt else None
         smem_peak = n_sms * clk_mhz / 1e3  # G wavefronts / s: one per SM per cycle
         smem_achieved = wav / (launch_ms / 1e3) / 1e9 if wav and launch_ms > 0 else None
-        roofline = {"bound": "alu", "kernel": "k_local_sort (sub-segment sort + count in shared memory, both passes)",
+        roofline = {"bound": "alu", "kernel": "k_local_sort (sub-segment sort + count in shared memory, all tiers)",
                     "achieved": achieved, "peak": peak_issue, "unit": "G warp-instructions/s",
                     "frac": achieved / peak_issue if achieved else None,
                     "traffic": cnt["dram"] * n_windows if cnt else None,
