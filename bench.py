@@ -347,7 +347,7 @@ def _mem_available() -> int:
 
 
 def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget: int,
-                 tune_trials: int = 8) -> dict:
+                 tune_trials: int = 8, fixed_rate: float = 0.0) -> dict:
     """The Poisson request stream, its inputs held in pinned host memory.
 
     The stream's inputs are generated up front.  When they would take more
@@ -355,7 +355,11 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
     pool and the tuner's trial batches need room beside them), the stream is
     run as consecutive blocks, each generated before it starts, at the same
     offered rate, and the latencies of all blocks are pooled; the line says how
-    many blocks were used."""
+    many blocks were used.
+
+    The offered rate is fixed_rate requests per second when it is set (the
+    workload's set arrival rate, the same in every run), else `load` times the
+    saturated rate measured on the first block."""
     import datagen
     params = datagen.served_request_params(n=n_req, scale=scale)
     need = sum(int(g * c * 1.06) + 4096 for (_, g, c, _, _, _) in params)  # bases + offsets
@@ -402,8 +406,8 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
             p0 = ctx.pack_stats()
             sat_b = closed_batch()
             sat_s += sat_b
-            if rate is None:
-                rate = load * len(jobs) / sat_b         # requests per second offered (first block)
+            if rate is None:                            # requests per second offered
+                rate = fixed_rate if fixed_rate > 0 else load * len(jobs) / sat_b
             gaps = np.random.default_rng(5 + bi).exponential(1.0 / rate, len(jobs))
             arrivals = np.cumsum(gaps) - gaps[0]
             tickets = []
@@ -434,7 +438,8 @@ def bench_served(hsk, device: int, n_req: int, scale: float, load: float, budget
                         f"x {scale:g}, coverage U[10, 30]x, 150 bp or 10 kb reads, k in {{21, 31, 55}}, filter [2,1000]",
             "n_requests": n_req, "n_windows": n, "generate_s": gen_s, "hbm_budget": budget,
             "blocks": n_blocks, "host_input_bytes": need,
-            "offered_rate_per_s": rate, "load": load,
+            "offered_rate_per_s": rate, "rate_fixed": fixed_rate > 0,
+            "load": rate * sat_s / n_req, "load_on_plain": rate * plain_s / n_req,
             "served": {"value_saturated": n / sat_s, "makespan_saturated_s": sat_s,
                        "value": n / open_s, "p50_ms": _pct(lat, 50) * 1e3, "p99_ms": _pct(lat, 99) * 1e3,
                        "p999_ms": _pct(lat, 99.9) * 1e3},
@@ -648,7 +653,9 @@ def main():
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--tune-trials", type=int, default=10, help="autotuner trials before the forms (0 = none)")
     ap.add_argument("--served-scale", type=float, default=1.0)
-    ap.add_argument("--served-load", type=float, default=0.7)
+    ap.add_argument("--served-load", type=float, default=0.7, help="offered load when --served-rate is 0")
+    ap.add_argument("--served-rate", type=float, default=150.0,
+                    help="Poisson arrival rate of the served stream, requests/s (0 = --served-load x saturated)")
     ap.add_argument("--served-budget", type=float, default=120e9)
     ap.add_argument("--ablations", action="store_true",
                     help="print one JSON line of bucketing diagnostics (bucket balance, m sweep) instead")
@@ -845,7 +852,7 @@ def main():
         torch.cuda.empty_cache()
         leg("batched", lambda: bench_batched(hsk, local, args.batched_sets, args.batched_scale, args.tune_trials))
         leg("served", lambda: bench_served(hsk, local, args.served_requests, args.served_scale, args.served_load,
-                                           int(args.served_budget), args.tune_trials))
+                                           int(args.served_budget), args.tune_trials, args.served_rate))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
