@@ -17,8 +17,8 @@
 // a read, buckets only partition the k-mers, and the output order is the
 // global key order of the set.
 //
-// A set whose keys do not all fit the on-chip sort (a sub-segment over the
-// second pass's capacity: repeat-rich input) is counted again alone through
+// A set whose keys do not all fit the on-chip sort (a sub-segment that no
+// on-chip tier nor the heavy-hitter lists take: repeat-rich input) is counted again alone through
 // the plain path, which handles that case; the pack's partial result for it
 // is dropped.
 #include <algorithm>
@@ -294,7 +294,7 @@ static int pack_pass(hsk_ctx* c, std::vector<PackSet*>& sets, const std::vector<
                     sub_off + 1, c->keys.p, c->d_err, expand_grid(c->num_sms), st);
         CK(cudaGetLastError());
         // S4/S5 on chip, statistics per set; the larger sub-segments take the
-        // second pass and the heavy-hitter k-mer lists (as in the plain path)
+        // larger on-chip tiers and the heavy-hitter k-mer lists (as in the plain path)
         CK(cudaMemsetAsync(c->d_nlocal, 0, 72, st));
         TRY(hsk_next_counter(c, st, &ctr));
         launch_local_sort(sub_off, nullptr, (uint32_t)NS, 0, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,

@@ -929,9 +929,9 @@ static int local_chunk(hsk_ctx* c, const Supermers& S, const std::vector<uint32_
                 sub_off + 1, c->keys.p, c->d_err, expand_grid(c->num_sms), st);
     CK(cudaGetLastError());
     prof_mark(c, st, 3);
-    // sort and count on chip; the sub-segments that do not fit go to a second
-    // pass with three times the capacity, then to heavy-hitter k-mer lists,
-    // and what none of these takes to the global radix passes
+    // sort and count on chip; the sub-segments that do not fit go to the
+    // larger tiers (1.5 and 3 times the capacity), then to heavy-hitter k-mer
+    // lists, and what none of these takes to the global radix passes
     CK(cudaMemsetAsync(c->d_nlocal, 0, 72, st));  // distinct, then {listed, keys} of the four steps
     TRY(hsk_next_counter(c, st, &ctr));
     launch_local_sort(sub_off, nullptr, (uint32_t)NS, 0, shift0, kw, c->keys.p, (uint32_t*)c->alt.p, kcv,

@@ -22,10 +22,13 @@
 //                     key in small bins, by one warp peeling off distinct keys
 //                     in larger ones), histogram, [lo, hi] filter; kept
 //                     (key, count) pairs written at the start of the
-//                     sub-segment's own range.  A second launch with one CTA
-//                     per SM and three times the capacity takes the
-//                     sub-segments that did not fit; what fits neither is
-//                     listed for the global path.
+//                     sub-segment's own range.  Launched in three tiers of
+//                     capacity: the sub-segments that do not fit tier 0 go
+//                     to tier 1 (1.5 times the capacity, two CTAs per SM),
+//                     what does not fit there to tier 2 (three times, one
+//                     CTA per SM); larger ones are heavy-hitter tasks
+//                     (k_heavy_count), and what fits nothing is listed for
+//                     the global path.
 //   k_compact      -- kept pairs of all sub-segments -> one output array.
 //   k_ov_gather    -- the listed sub-segments' keys -> one array for the
 //                     global path.
@@ -1012,8 +1015,8 @@ void launch_local_sort(const uint64_t* sub_off, const uint32_t* only, uint32_t n
 // holds heavy hitters (many copies of a few k-mers, from genomic repeats);
 // such a task is transformed into a k-mer list -- one (k-mer, count) tuple
 // per distinct k-mer -- instead of being counted the normal way.  Here the
-// tasks are the sub-segments, a heavy one is one over the first pass's
-// on-chip capacity (about three times the mean sub-segment), and since a
+// tasks are the sub-segments, a heavy one is one over the largest on-chip
+// tier's capacity (about nine times the mean sub-segment), and since a
 // sub-segment holds every copy of each of its k-mers, its k-mer list is the
 // exact count: one CTA folds the sub-segment's keys into a shared-memory table
 // (open addressing, a 64-bit compare-and-swap claims a slot, an atomic add
