@@ -55,7 +55,7 @@ NCU_PER_KEY = {
     # long-read workload, k=31: k_local_sort tiers 0, 1 and 2 (the heavy-hitter kernel does not
     # run at this scale), smsp__inst_executed.sum, DRAM bytes and shared-memory wavefronts
     # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) from the 0.1-scale case (149.6 M keys)
-    ("long_read", "bebf6f76bbefbe71"): {"inst": 10.1611, "dram": 8.3749, "smem_wavefronts": 2.2143},
+    ("long_read", "f80c337d588545af"): {"inst": 10.1611, "dram": 8.3749, "smem_wavefronts": 2.2143},
 }
 # Warp schedulers per SM (Blackwell): each issues at most one warp instruction
 # per cycle; the issue peak is SMs (queried from the device) x this x the SM
