@@ -44,8 +44,8 @@ METRIC = "k-mers counted/s at k=31 on 1 GB300 (plain vs batched/served); p50/p99
 UNIT = "k-mers/s"
 
 # Per-key counters of the dominant kernel from one ncu capture, keyed by the
-# workload and the SHA-256 (first 16 hex digits) of the kernel's source file
-# at capture time; used only while that source is unchanged.
+# workload and the SHA-256 (first 16 hex digits) of the kernel's source code
+# (comments stripped) at capture time; used only while that code is unchanged.
 #   inst  : warp instructions issued per key (all on-chip tiers)
 #   dram  : DRAM bytes read + written per key (all tiers)
 #   smem_wavefronts : shared-memory wavefronts per key (all tiers); an SM's
@@ -55,7 +55,7 @@ NCU_PER_KEY = {
     # long-read workload, k=31: k_local_sort tiers 0, 1 and 2 (the heavy-hitter kernel does not
     # run at this scale), smsp__inst_executed.sum, DRAM bytes and shared-memory wavefronts
     # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) from the 0.1-scale case (149.6 M keys)
-    ("long_read", "f80c337d588545af"): {"inst": 10.1611, "dram": 8.3749, "smem_wavefronts": 2.2143},
+    ("long_read", "068cb6efb5eb6836"): {"inst": 10.1611, "dram": 8.3749, "smem_wavefronts": 2.2143},
 }
 # Warp schedulers per SM (Blackwell): each issues at most one warp instruction
 # per cycle; the issue peak is SMs (queried from the device) x this x the SM
@@ -64,7 +64,14 @@ SCHEDULERS_PER_SM = 4
 
 
 def source_sha(path: str) -> str:
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    """SHA-256 (16 hex digits) of a CUDA source's code: comments and
+    whitespace-only differences do not change it, any code change does."""
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+    text = re.sub(r"//[^\n]*", "", text)                  # line comments
+    text = "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def host_cpu() -> dict:
