@@ -391,9 +391,12 @@ uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k) {
     if (c->cfg.n_buckets) return c->cfg.n_buckets;
     // small jobs: fewer buckets keep the per-CTA tables cheap
     if (n_bases < (1ull << 22)) return 256;
-    // 128-bit keys: the on-chip sort holds half as many keys per sub-segment,
-    // so large jobs need twice the groups
-    const uint32_t B = (k > 32 && c->cfg.local_sort) ? 8192 : 4096;
+    // 4096 buckets for both key widths.  128-bit keys fit half as many per
+    // sub-segment, but twice the groups (8192 buckets) measured slower on the
+    // short-read workload (about 1 ms) since larger sub-segments go to the
+    // middle on-chip tier instead of the one-CTA tier
+    (void)k;
+    const uint32_t B = 4096;
     return c->tune.plain_bucket_shift ? std::max<uint32_t>(256, B >> c->tune.plain_bucket_shift) : B;
 }
 
