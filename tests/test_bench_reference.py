@@ -28,3 +28,25 @@ def test_reference_arm_prints_one_json_line():
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert d["config"]["k"] == 31 and d["config"]["workload"].startswith("tiny")
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_counter_key_ignores_comments_but_not_code(tmp_path):
+    """The per-key ncu counters are keyed to the kernel source's code: a comment
+    or whitespace edit keeps the key, any code edit changes it."""
+    b = _bench_module()
+    src = "// header\nint f(int x) {  /* doubled */\n    return 2 * x;  // twice\n}\n"
+    a = tmp_path / "a.cu"
+    a.write_text(src)
+    base = b.source_sha(str(a))
+    a.write_text("// another header\n\nint f(int x) {\n    return 2 *   x;  // times two\n}\n")
+    assert b.source_sha(str(a)) == base
+    a.write_text(src.replace("2 * x", "3 * x"))
+    assert b.source_sha(str(a)) != base
