@@ -176,7 +176,9 @@ int hsk_result_copy(hsk_ctx* ctx, const hsk_result* res, uint64_t* kmers_dst, ui
  * 2^28 bases by default (the autotuner picks both), by one pass of the
  * pipeline: their bases share one device buffer, each job owns a range of
  * minimizer buckets, and every launch serves all of them (Sec. 3.4's
- * independent tasks on shared workers).  Larger jobs run alone.  Each outs[i]
+ * independent tasks on shared workers).  Larger jobs run alone, on their
+ * slot's highest-priority stream, so packs on the other slots fill the gaps
+ * around them instead of slowing them down.  Each outs[i]
  * is bit-identical to what hsk_count() returns for jobs[i] alone, except
  * n_supermers and device_ms, which describe the pass that counted it (a
  * packed pass forms supermers with its own bucket count and times all its
@@ -230,7 +232,9 @@ int hsk_tune_set(hsk_ctx* ctx, const hsk_tune_result* params);
 /* Served form (continuous batching).  hsk_submit queues a job and returns a
  * ticket at once; a worker thread admits queued jobs while the device memory
  * they need fits the budget, runs admitted jobs concurrently on their own
- * streams, and completes them in any order.  Inputs stay borrowed until the
+ * streams (small jobs of one k, m, lo and hi packed into shared passes as in
+ * hsk_count_batch; a job too large to pack on its slot's highest-priority
+ * stream), and completes them in any order.  Inputs stay borrowed until the
  * job completes.  hsk_poll sets *done to 1 when the ticket's job finished;
  * hsk_wait blocks until then and fills *out (host arrays owned by the context,
  * valid until hsk_release(ticket)); hsk_cancel withdraws a job that has not
