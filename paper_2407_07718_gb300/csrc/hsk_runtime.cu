@@ -392,9 +392,9 @@ uint32_t hsk_pick_buckets(hsk_ctx* c, uint64_t n_bases, int k) {
     // small jobs: fewer buckets keep the per-CTA tables cheap
     if (n_bases < (1ull << 22)) return 256;
     // 4096 buckets for both key widths.  128-bit keys fit half as many per
-    // sub-segment, but twice the groups (8192 buckets) measured slower on the
-    // short-read workload (about 1 ms) since larger sub-segments go to the
-    // middle on-chip tier instead of the one-CTA tier
+    // sub-segment, but twice the groups (8192 buckets) measured about 1 ms
+    // slower on the short-read workload once the middle on-chip tier took
+    // the sub-segments over the first tier's capacity
     (void)k;
     const uint32_t B = 4096;
     return c->tune.plain_bucket_shift ? std::max<uint32_t>(256, B >> c->tune.plain_bucket_shift) : B;

@@ -164,7 +164,9 @@ __device__ __forceinline__ void record_top_digits(const u64 (&W)[4], uint32_t n,
 // group tile_seg[g] and is tile g - tile_base[group] of it.
 // MODE 0: sub_cnt[c * 256 + d] += keys of group c whose digit at `shift` is d.
 //         Thread t holds records t, t + 256, ... of the tile (EXP_RPT of
-//         them) and rolls through their k-mers (record_kmers).
+//         them) and rolls through their k-mers: only the first and last four
+//         bases when the digit is the key's top one (record_top_digits),
+//         else the whole codes (record_kmers).
 // MODE 1: every key to keys_out[cursor[c * 256 + d]++] (a reservation per
 //         digit and round), never past sub_end[c * 256 + d].  The tile's
 //         records are staged in shared memory with the prefix of their k-mer

@@ -411,7 +411,7 @@ static void launch_mode(const SmParams& p, cudaStream_t st) {
     do {                                                                                     \
         auto fn = p.lexical ? k_supermer<MODE, W, NR, true> : k_supermer<MODE, W, NR, false>; \
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cap);  \
-        fn<<<grid, SM_WARPS * 32, sm, st>>>(p);                                                        \
+        fn<<<grid, SM_WARPS * 32, sm, st>>>(p);                                              \
     } while (0)
     if (!wide && nreg == 2) HSK_SM_LAUNCH(false, 2);
     else if (!wide) HSK_SM_LAUNCH(false, 3);
