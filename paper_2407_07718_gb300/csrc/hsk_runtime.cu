@@ -1198,7 +1198,12 @@ int hsk_count_host_on(hsk_ctx* c, const char* reads, const uint64_t* offsets, ui
     if (n_bases >= (64ull << 20) && c->cstream) {
         const int n = (int)std::min<uint64_t>(HSK_MAX_PIPE, std::max<uint64_t>(2, n_bases >> 27));
         pipe.n = n;
-        for (int i = 0; i < n; ++i) pipe.bound[i] = ((uint64_t)i * n_bases / n) & ~0xFFFFull;
+        // a short first chunk, so that S1/S2 start soon after the call, then
+        // equal chunks (bounds on 64 K-base multiples)
+        const uint64_t first = std::max<uint64_t>(1ull << 20, n_bases / (4 * (uint64_t)n));
+        pipe.bound[0] = 0;
+        for (int i = 1; i < n; ++i)
+            pipe.bound[i] = (first + (uint64_t)(i - 1) * (n_bases - first) / (uint64_t)(n - 1)) & ~0xFFFFull;
         pipe.bound[n] = n_bases;
         for (int i = 0; i < n; ++i) pipe.ev[i] = c->pipe_ev[i];
         pipe.h_reads = reads;
